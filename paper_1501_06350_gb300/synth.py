@@ -1,0 +1,320 @@
+"""Seeded synthetic inputs for the D-Iteration solver and its oracle.
+
+This module only draws graphs, teleport vectors and edge-change batches. It holds
+none of the method's arithmetic (no diffusion matrix, no fluid, no history), so
+that the CUDA path and the CPU oracle can both be fed from it without sharing
+any code that computes a result.
+
+The paper's measurements use a crawl of the .uk web domain (Section 4: 133 M
+pages, 5.5 B links). That dataset is not available here; the generators below
+stand in for it with the structure that matters to a push-diffusion solver:
+
+* ``pa_graph``   -- out-degrees drawn from a truncated Zipf law, targets chosen
+  by sequential preferential attachment on in-degree, a fraction of dangling
+  pages (no out-links).  Small graphs (about 10^4 nodes).
+* ``web_graph``  -- pages grouped into hosts of lognormal size, most links
+  internal to the host (the locality noted in Section 2.5), power-law
+  in-degree through Chung-Lu attractiveness with a Pareto tail, Zipf
+  out-degrees with a wide clip (hub pages), dangling pages.
+
+All graphs are returned as a raw out-CSR ``(ptr int64[n+1], idx int32[nnz])``
+whose rows are *not* sorted and may contain duplicate links, exactly what a
+crawler would hand over; building the canonical diffusion structure out of it
+is the solver's job (and the oracle's, independently).
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+#: Base of every seed used by the test-suite and the benchmark.
+SEED_BASE = 150106350
+
+
+@dataclasses.dataclass
+class RawGraph:
+    n: int
+    ptr: np.ndarray          # int64 [n+1]
+    idx: np.ndarray          # int32 [nnz]
+    w: np.ndarray | None     # float32/float64 [nnz] or None (unweighted)
+    meta: dict
+
+    @property
+    def nnz(self) -> int:
+        return int(self.ptr[-1])
+
+
+def rng_for(seed_offset: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(SEED_BASE + int(seed_offset)))
+
+
+def zipf_degrees(rng: np.random.Generator, count: int, alpha: float, lo: int, hi: int,
+                 target_sum: int | None) -> np.ndarray:
+    """Draw ``count`` degrees with P(k) proportional to k^-alpha on [lo, hi].
+
+    When ``target_sum`` is given, every draw is scaled by one common factor with
+    stochastic rounding and clipped back to [lo, hi]; the factor is found by
+    bisection so that the realised sum lands within 1% of the target.
+    """
+    if count == 0:
+        return np.zeros(0, dtype=np.int64)
+    k = np.arange(lo, hi + 1, dtype=np.float64)
+    cdf = np.cumsum(k ** (-alpha))
+    cdf /= cdf[-1]
+    raw = k[np.minimum(np.searchsorted(cdf, rng.random(count), side="right"), len(k) - 1)]
+    if target_sum is None:
+        return raw.astype(np.int64)
+    u = rng.random(count)
+
+    def realise(s: float) -> np.ndarray:
+        return np.clip(np.floor(raw * s + u), lo, hi).astype(np.int64)
+
+    a, b = 1e-3, 1e4
+    for _ in range(80):
+        m = math.sqrt(a * b)
+        if realise(m).sum() < target_sum:
+            a = m
+        else:
+            b = m
+    return realise(b)
+
+
+def pa_graph(n: int = 10_000, m_target: int = 100_000, dangling_frac: float = 0.10,
+             alpha: float = 2.1, deg_hi: int = 1000, seed_offset: int = 1) -> RawGraph:
+    """Preferential-attachment graph: Zipf out-degrees, targets by a Polya urn.
+
+    Each link picks its target with probability proportional to (in-degree + 1)
+    at the moment it is drawn (links are drawn source by source, in id order).
+    Self-links are redrawn; duplicate links are kept (the builders merge them).
+    """
+    rng = rng_for(seed_offset)
+    n_dang = int(round(dangling_frac * n))
+    dang = np.zeros(n, dtype=bool)
+    dang[rng.permutation(n)[:n_dang]] = True
+    deg = np.zeros(n, dtype=np.int64)
+    deg[~dang] = zipf_degrees(rng, int((~dang).sum()), alpha, 1, min(deg_hi, max(n - 1, 1)),
+                              m_target)
+    if n == 1:
+        deg[:] = 0
+    m = int(deg.sum())
+    urn = np.empty(n + m, dtype=np.int64)
+    urn[:n] = np.arange(n)
+    ulen = n
+    idx = np.empty(m, dtype=np.int32)
+    draws = rng.random(4 * m + 16)
+    di = 0
+    e = 0
+    for src in range(n):
+        for _ in range(int(deg[src])):
+            while True:
+                if di >= len(draws):
+                    draws = rng.random(4 * m + 16)
+                    di = 0
+                t = int(urn[int(draws[di] * ulen)])
+                di += 1
+                if t != src:
+                    break
+            idx[e] = t
+            e += 1
+            urn[ulen] = t
+            ulen += 1
+    ptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(deg, out=ptr[1:])
+    return RawGraph(n, ptr, idx, None,
+                    dict(kind="pa", n=n, raw_nnz=m, dangling=n_dang, alpha=alpha, deg_hi=deg_hi,
+                         seed=SEED_BASE + seed_offset))
+
+
+def web_graph(n: int = 4_000_000, m_target: int = 40_000_000, dangling_frac: float = 0.15,
+              host_mean: float = 100.0, host_sigma: float = 1.0, intra: float = 0.80,
+              in_tail: float = 1.1, alpha: float = 2.1, deg_hi: int = 50_000,
+              weighted: str | None = None, seed_offset: int = 2) -> RawGraph:
+    """Host-structured web-like graph (Chung-Lu targets within and across hosts).
+
+    * host sizes ~ lognormal with the given mean and log-sd, consecutive ids;
+    * attractiveness a_v ~ Pareto(x_min=1, tail ``in_tail``), which gives an
+      in-degree power law with exponent 1 + in_tail;
+    * a fraction ``intra`` of links picks its target inside the source's host
+      with probability proportional to a_v, the rest over the whole graph;
+    * ``dangling_frac`` of the pages have no out-link; the others draw Zipf
+      out-degrees on [1, deg_hi] rescaled to hit ``m_target`` links;
+    * ``weighted``: None, "lognormal32" (lognormal(0,1) in float32) or
+      "lognormal64".
+    """
+    rng = rng_for(seed_offset)
+    mu = math.log(host_mean) - 0.5 * host_sigma ** 2
+    sizes = []
+    tot = 0
+    while tot < n:
+        s = np.maximum(1, np.round(rng.lognormal(mu, host_sigma, size=max(16, n // 50))))
+        s = s.astype(np.int64)
+        sizes.append(s)
+        tot += int(s.sum())
+    sizes = np.concatenate(sizes)
+    csz = np.cumsum(sizes)
+    nh = int(np.searchsorted(csz, n, side="left")) + 1
+    sizes = sizes[:nh].copy()
+    sizes[-1] -= int(csz[nh - 1] - n)
+    hstart = np.zeros(nh + 1, dtype=np.int64)
+    np.cumsum(sizes, out=hstart[1:])
+    host_of = np.repeat(np.arange(nh, dtype=np.int64), sizes)
+
+    attract = (1.0 - rng.random(n)) ** (-1.0 / in_tail)
+    cum = np.zeros(n + 1, dtype=np.float64)
+    np.cumsum(attract, out=cum[1:])
+
+    n_dang = int(round(dangling_frac * n))
+    dang = np.zeros(n, dtype=bool)
+    dang[rng.permutation(n)[:n_dang]] = True
+    deg = np.zeros(n, dtype=np.int64)
+    # rows must be drawable without repeats: clip at half the page count
+    deg[~dang] = zipf_degrees(rng, int((~dang).sum()), alpha, 1, min(deg_hi, max((n - 1) // 2, 1)),
+                              m_target)
+    if n == 1:
+        deg[:] = 0
+    m = int(deg.sum())
+    src = np.repeat(np.arange(n, dtype=np.int64), deg)
+    h = host_of[src]
+    lo = cum[hstart[h]]
+    hi = cum[hstart[h + 1]]
+    single = sizes[h] <= 1
+    is_intra = (rng.random(m) < intra) & ~single
+    u = rng.random(m)
+    val = np.where(is_intra, lo + u * (hi - lo), u * cum[n])
+    tgt = np.searchsorted(cum, val, side="right") - 1
+    tgt = np.clip(tgt, 0, n - 1)
+    # A page links to distinct pages: redraw self-links and repeated links of a
+    # row (inside the host for the first rounds, then across the graph, and
+    # finally uniformly, which always terminates).
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(deg, out=rowptr[1:])
+    sub = np.arange(m, dtype=np.int64)          # links whose rows are re-checked
+    for it in range(40):
+        key = src[sub] * n + tgt[sub]
+        order = np.argsort(key, kind="stable")
+        ks = key[order]
+        dup = np.zeros(len(sub), dtype=bool)
+        dup[order[1:]] = ks[1:] == ks[:-1]
+        bad = sub[np.nonzero(dup | (tgt[sub] == src[sub]))[0]]
+        if len(bad) == 0:
+            break
+        uu = rng.random(len(bad))
+        if it < 4:
+            vv = np.where(is_intra[bad], lo[bad] + uu * (hi[bad] - lo[bad]), uu * cum[n])
+            tgt[bad] = np.clip(np.searchsorted(cum, vv, side="right") - 1, 0, n - 1)
+        elif it < 12:
+            tgt[bad] = np.clip(np.searchsorted(cum, uu * cum[n], side="right") - 1, 0, n - 1)
+        else:
+            tgt[bad] = rng.integers(0, n, size=len(bad))
+        rows = np.unique(src[bad])
+        lens = rowptr[rows + 1] - rowptr[rows]
+        starts = np.repeat(rowptr[rows] - np.concatenate([[0], np.cumsum(lens)[:-1]]), lens)
+        sub = starts + np.arange(int(lens.sum()), dtype=np.int64)
+    ptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(deg, out=ptr[1:])
+    w = None
+    if weighted == "lognormal32":
+        w = rng.lognormal(0.0, 1.0, size=m).astype(np.float32)
+    elif weighted == "lognormal64":
+        w = rng.lognormal(0.0, 1.0, size=m).astype(np.float64)
+    elif weighted is not None:
+        raise ValueError(weighted)
+    return RawGraph(n, ptr, tgt.astype(np.int32), w,
+                    dict(kind="web", n=n, raw_nnz=m, hosts=nh, dangling=n_dang, intra=intra,
+                         in_tail=in_tail, alpha=alpha, deg_hi=deg_hi, weighted=weighted,
+                         seed=SEED_BASE + seed_offset))
+
+
+def small_graph(n: int, m: int, seed_offset: int, dangling_frac: float = 0.1,
+                self_loops: bool = False, weighted: bool = False) -> RawGraph:
+    """Uniform random multigraph for unit tests (optional self-links and weights)."""
+    rng = rng_for(1000 + seed_offset)
+    src = rng.integers(0, n, size=m)
+    dst = rng.integers(0, n, size=m)
+    if n > 1 and dangling_frac > 0:
+        dang = rng.random(n) < dangling_frac
+        keep = ~dang[src]
+        src, dst = src[keep], dst[keep]
+    if not self_loops and n > 1:
+        keep = src != dst
+        src, dst = src[keep], dst[keep]
+    order = np.argsort(src, kind="stable")
+    src, dst = src[order], dst[order]
+    ptr = np.zeros(n + 1, dtype=np.int64)
+    np.add.at(ptr, src + 1, 1)
+    ptr = np.cumsum(ptr)
+    w = rng.lognormal(0.0, 1.0, size=len(dst)) if weighted else None
+    return RawGraph(n, ptr, dst.astype(np.int32), w, dict(kind="small", n=n))
+
+
+def edges_from_csr(g: RawGraph) -> tuple[np.ndarray, np.ndarray]:
+    """Expand a CSR into (src, dst) arrays in input order."""
+    src = np.repeat(np.arange(g.n, dtype=np.int64), np.diff(g.ptr))
+    return src, g.idx.astype(np.int64)
+
+
+def to_csc(g: RawGraph) -> RawGraph:
+    """Re-express the same link multiset as an in-edge CSR (ptr over targets).
+
+    Within each target row the sources keep input order; this is a pure
+    re-indexing of the input and is used to feed the CSC entry of the builders.
+    """
+    src, dst = edges_from_csr(g)
+    order = np.argsort(dst, kind="stable")
+    ptr = np.zeros(g.n + 1, dtype=np.int64)
+    np.add.at(ptr, dst + 1, 1)
+    ptr = np.cumsum(ptr)
+    w = None if g.w is None else g.w[order]
+    return RawGraph(g.n, ptr, src[order].astype(np.int32), w, dict(g.meta, layout="csc"))
+
+
+def uniform_z(n: int) -> np.ndarray:
+    return np.full(n, 1.0 / n, dtype=np.float64)
+
+
+def random_z(n: int, seed_offset: int, signed: bool = False) -> np.ndarray:
+    rng = rng_for(2000 + seed_offset)
+    z = rng.random(n)
+    if signed:
+        z = z - 0.3
+    return z / np.abs(z).sum()
+
+
+def seed_set_z(n: int, n_seeds: int, seed_offset: int) -> np.ndarray:
+    """Personalised teleport vector: uniform over ``n_seeds`` random seed pages."""
+    rng = rng_for(3000 + seed_offset)
+    z = np.zeros(n, dtype=np.float64)
+    z[rng.choice(n, size=min(n_seeds, n), replace=False)] = 1.0 / min(n_seeds, n)
+    return z
+
+
+def edge_batch(g_canon_ptr: np.ndarray, g_canon_idx: np.ndarray, n: int, frac: float,
+               seed_offset: int, insert_share: float = 0.5) -> tuple[np.ndarray, np.ndarray, np.ndarray]:
+    """Random link changes: ``frac`` of the current links, half deletions of existing
+    links and half insertions of new (src, dst) pairs, src != dst.
+
+    Returns (src int32, dst int32, op int8) with op = +1 insert, -1 delete, in
+    random order.  Insertions may hit links that already exist and deletions
+    are drawn from existing links, so both the no-op and the effective cases
+    occur.
+    """
+    rng = rng_for(4000 + seed_offset)
+    nnz = int(g_canon_ptr[-1])
+    m = max(1, int(round(frac * max(nnz, 1))))
+    n_ins = int(round(insert_share * m))
+    n_del = m - n_ins if nnz > 0 else 0
+    src_e = np.repeat(np.arange(n, dtype=np.int64), np.diff(g_canon_ptr))
+    pick = rng.integers(0, max(nnz, 1), size=n_del)
+    ds, dd = src_e[pick], g_canon_idx[pick].astype(np.int64)
+    is_ = rng.integers(0, n, size=n_ins)
+    id_ = rng.integers(0, n, size=n_ins)
+    if n > 1:
+        same = is_ == id_
+        id_[same] = (id_[same] + 1) % n
+    src = np.concatenate([ds, is_])
+    dst = np.concatenate([dd, id_])
+    op = np.concatenate([-np.ones(n_del, np.int8), np.ones(n_ins, np.int8)])
+    perm = rng.permutation(len(src))
+    return src[perm].astype(np.int32), dst[perm].astype(np.int32), op[perm]
