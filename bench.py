@@ -1,0 +1,343 @@
+#!/usr/bin/env python
+"""Benchmark of the D-Iteration hot path on one GB300 (or N replicas under torchrun).
+
+Workload: the host-structured web-like graph (4,000,000 pages, 40,000,000 links,
+hosts of lognormal size with mean 100, 80% intra-host links, Pareto(1.1)
+attractiveness, 15% dangling pages, Zipf(2.1) out-degrees clipped to
+[1, 50000]), d = 0.85, uniform Z, tol = 1e-9 on |F|_1 / (1 - d).
+
+One step = the whole hot path on that graph: a from-scratch solve to tol
+(init, frontier sweeps, stop test), then a 1% link-change batch (half
+deletions, half insertions) applied by correction-fluid injection and
+re-converged, then the inverse batch applied and re-converged, which leaves
+the graph as it started.  The metric is edge pushes per second over the step
+(links pushed by all three solves / step time); the from-scratch time to tol
+is reported beside it.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle
+(sequential FP64 DI-argmax) on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1501_06350_gb300 import synth  # noqa: E402
+
+D = 0.85
+TOL = 1e-9
+BATCH_FRAC = 0.01
+METRIC = "edge-pushes/s"
+WORKLOAD = ("web-like graph: 4,000,000 pages, 40,000,000 links, hosts lognormal(mean 100), "
+            "80% intra-host links, Pareto(1.1) attractiveness, 15% dangling, Zipf(2.1) out-degree "
+            "in [1,50000]; d=0.85, uniform Z, plain FP64 solve to |F|_1/(1-d) <= 1e-9, then a 1% "
+            "link-update round trip (inject + re-converge, twice)")
+GEN_KW = dict(n=4_000_000, m_target=40_000_000)
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def load_workload(small: bool):
+    kw = dict(n=200_000, m_target=2_000_000) if small else GEN_KW
+    t = time.time()
+    g = synth.cached(synth.web_graph, **kw)
+    log(f"[bench] workload n={g.n} raw links={g.nnz} ready in {time.time() - t:.1f}s")
+    return g
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"di_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------ reference arm
+def run_reference(args, g):
+    import oracle
+    oracle.build()
+    cp, ci, _ = oracle.canonical_csr(g.n, g.ptr, g.idx)
+    rounds = 3  # one round = n elementary diffusions (Section 4.2)
+    cap = rounds * g.n
+    times, pushes = [], []
+    for k in range(args.warmup + args.steps):
+        t = time.perf_counter()
+        _, _, info, _ = oracle.di_solve(g.n, cp, ci, None, D, None, tol=TOL, max_diffusions=cap)
+        dt = time.perf_counter() - t
+        if k >= args.warmup:
+            times.append(dt)
+            pushes.append(info["edge_pushes"])
+    val = sum(pushes) / sum(times)
+    sample = (f"sequential FP64 DI-argmax oracle, first {rounds} rounds ({cap} diffusions) of the "
+              f"from-scratch solve per step, 1 thread")
+    return {"impl": "reference", "metric": METRIC, "value": val, "unit": METRIC, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_dict(g, None),
+            "cpu_baseline": {"value": val, "unit": METRIC, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": val, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def config_dict(g, gi):
+    c = {"workload": WORKLOAD, "n": g.n, "links": gi["nnz"] if gi else None, "d": D, "tol": TOL,
+         "z": "uniform", "batch_frac": BATCH_FRAC, "parallelism": "replicas (one independent solve per GPU)",
+         "l2": "inputs larger than L2 (160 MB of link targets); L2 flushed (256 MB write) between steps"}
+    if gi:
+        c["dangling"] = gi["n_dangling"]
+    return c
+
+
+def cpu_baseline(g, cp, ci):
+    import oracle
+    oracle.build()
+    t = time.perf_counter()
+    _, _, info, _ = oracle.di_solve(g.n, cp, ci, None, D, None, tol=TOL)
+    dt = time.perf_counter() - t
+    return {"value": info["edge_pushes"] / dt, "unit": METRIC, "cores": 1, "kind": "oracle",
+            "sample": ("one full from-scratch solve of the same graph to |F|_1/(1-d) <= 1e-9 by the "
+                       "sequential FP64 DI-argmax oracle (no update round trip)"),
+            "time_to_tol_s": dt, "edge_pushes": info["edge_pushes"], "diffusions": info["diffusions"]}
+
+
+def traffic_for(kernel_src: str):
+    """DRAM traffic per push launch from the committed ncu summary, if it was
+    taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "push_web4m_traffic.json")
+    if not os.path.exists(path):
+        return None
+    rec = json.load(open(path))
+    h = hashlib.sha1(open(kernel_src, "rb").read()).hexdigest()
+    return rec.get("dram_bytes_per_launch") if rec.get("source_sha1") == h else None
+
+
+# ------------------------------------------------------------------ main
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--small", action="store_true", help="200k-page graph (quick check)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and not args.small:
+        ap.error("--warmup must be >= 3")
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        g = load_workload(args.small)
+        print(json.dumps(run_reference(args, g)), flush=True)
+        return 0
+
+    import torch
+    import torch.distributed as dist
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1501_06350_gb300 import _lib, di
+
+    g = load_workload(args.small)
+    G = di.Graph(g.n, g.ptr, g.idx)
+    gi = G.info()
+    cp, ci, _ = G.export_csr()
+    src, dst, op = synth.exact_batch(cp, ci, g.n, BATCH_FRAC, 1)
+    bs, bd, bo = (torch.from_numpy(x).cuda() for x in (src, dst, op))
+    bo_inv = -bo
+    st = di.State(G)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    L = _lib.lib()
+
+    def step():
+        H, i1 = st.solve(D, tol=TOL)
+        st.update_edges(bs, bd, bo)
+        H, i2 = st.resume(tol=TOL)
+        st.update_edges(bs, bd, bo_inv)
+        H, i3 = st.resume(tol=TOL)
+        assert i1["converged"] and i2["converged"] and i3["converged"], (i1, i2, i3)
+        return i1, i2, i3
+
+    for _ in range(args.warmup):
+        step()
+        flush.zero_()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    launches0 = L.di_kernel_launches()
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter()
+    infos = []
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record()
+        _, i1 = st.solve(D, tol=TOL)
+        ev[k][1].record()
+        st.update_edges(bs, bd, bo)
+        _, i2 = st.resume(tol=TOL)
+        st.update_edges(bs, bd, bo_inv)
+        _, i3 = st.resume(tol=TOL)
+        ev[k][2].record()
+        infos.append((i1, i2, i3))
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t_wall
+    launches = L.di_kernel_launches() - launches0
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(c) for a, b, c in ev]
+    solve_ms = [a.elapsed_time(b) for a, b, c in ev]
+    pushes = sum(i1["edge_pushes"] + i2["edge_pushes"] + i3["edge_pushes"] for i1, i2, i3 in infos)
+    t_local = sum(step_ms) / 1e3
+    t_max = t_local
+    pushes_all = pushes
+    if world > 1:
+        tt = torch.tensor([t_local], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+        pp = torch.tensor([pushes], dtype=torch.float64, device="cuda")
+        dist.all_reduce(pp)
+        pushes_all = float(pp.item())
+    value = pushes_all / t_max
+
+    # roofline of the dominant kernel (push), CUDA events around each launch
+    _, prof = st.solve(D, tol=TOL, profile=1)
+    per_launch_links = prof["push_edges"] / max(prof["push_launches"], 1)
+    push_avg_s = prof["push_ms"] / 1e3 / max(prof["push_launches"], 1)
+    alg_bytes = 12.0 * per_launch_links
+    peaks = {}
+    pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk_path):
+        peaks = json.load(open(pk_path))
+    peak = peaks.get("hbm_gbs", 6800.0)
+    achieved = alg_bytes / push_avg_s / 1e9
+    traffic = traffic_for(os.path.join(ROOT, "paper_1501_06350_gb300", "csrc", "di_solve.cu"))
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "kernel": "k_push", "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+                "algorithmic_bytes_per_launch": alg_bytes, "links_per_launch": per_launch_links,
+                "launches": prof["push_launches"], "push_ms_avg": 1e3 * push_avg_s,
+                "push_share_of_solve": prof["push_ms"] / prof["time_ms"] if prof["time_ms"] else None}
+
+    solve_pushes = statistics.median([i1["edge_pushes"] for i1, _, _ in infos])
+    out = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": config_dict(g, gi),
+           "time_to_tol_ms": statistics.median(solve_ms),
+           "solve": {"edge_pushes": solve_pushes, "sweeps": statistics.median([i1["sweeps"] for i1, _, _ in infos]),
+                     "edge_pushes_per_s": solve_pushes / (statistics.median(solve_ms) / 1e3),
+                     "rounds_equiv": solve_pushes / gi["nnz"]},
+           "update": {"ms": statistics.median([s - v for s, v in zip(step_ms, solve_ms)]),
+                      "batch_links": int(len(src)),
+                      "reconverge_pushes": statistics.median([i2["edge_pushes"] + i3["edge_pushes"] for _, i2, i3 in infos])},
+           "wall_s": wall, "gpu_launches": int(launches), "clocks": clk, "roofline": roofline}
+
+    if rank == 0 and world == 1 and not args.no_e2e:
+        out["e2e"] = e2e(args, g, src, dst, op, di, torch)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(g, cp, ci)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def e2e(args, g, src, dst, op, di, torch):
+    """Same step through the public API with host buffers: graph upload from
+    pinned host memory, host Z in, host H out after every solve."""
+    def pinned(a):
+        t = torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        return t.numpy()
+    ptr, idx = pinned(g.ptr), pinned(g.idx)
+    Z = pinned(np.full(g.n, 1.0 / g.n))
+    s, d_, o, oi = pinned(src), pinned(dst), pinned(op), pinned(-op)
+    Hh = pinned(np.zeros(g.n))
+    times, pushes = [], []
+    for k in range(2 + max(1, min(args.steps, 3))):
+        t = time.perf_counter()
+        G = di.Graph(g.n, ptr, idx)
+        st = di.State(G)
+        _, i1 = st.solve(D, Z=Z, tol=TOL, out=Hh, device=False)
+        st.update_edges(s, d_, o)
+        _, i2 = st.resume(tol=TOL, out=Hh, device=False)
+        st.update_edges(s, d_, oi)
+        _, i3 = st.resume(tol=TOL, out=Hh, device=False)
+        dt = time.perf_counter() - t
+        st.close()
+        G.close()
+        if k >= 2:
+            times.append(dt)
+            pushes.append(i1["edge_pushes"] + i2["edge_pushes"] + i3["edge_pushes"])
+    h2d = ptr.nbytes + idx.nbytes + Z.nbytes + 2 * (s.nbytes + d_.nbytes + o.nbytes)
+    d2h = 3 * Hh.nbytes
+    return {"value": sum(pushes) / sum(times), "unit": METRIC, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * sum(times) / len(times),
+            "includes": "graph build from pinned host CSR, state setup, 3 solves with host Z/H, 2 updates"}
+
+
+if __name__ == "__main__":
+    sys.exit(main())

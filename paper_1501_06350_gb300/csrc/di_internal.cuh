@@ -1,0 +1,196 @@
+// Internal declarations shared by the translation units of libdi.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/di.h"
+
+namespace di {
+
+// ---------------------------------------------------------------- errors
+struct Err {
+    di_status st;
+};
+
+di_status note_cuda(cudaError_t e);          // records e for di_last_cuda_error()
+#define DI_CUDA(call)                                                      \
+    do {                                                                   \
+        cudaError_t _e = (call);                                           \
+        if (_e != cudaSuccess) return ::di::note_cuda(_e);                 \
+    } while (0)
+#define DI_TRY(call)                                                       \
+    do {                                                                   \
+        di_status _s = (call);                                             \
+        if (_s != DI_OK) return _s;                                        \
+    } while (0)
+
+// Stream-ordered device allocation; returns DI_ERR_OOM on failure.
+di_status dalloc(void **p, size_t bytes, cudaStream_t s);
+void dfree(void *p, cudaStream_t s);
+
+template <typename T>
+di_status dalloc_t(T **p, size_t count, cudaStream_t s)
+{
+    return dalloc(reinterpret_cast<void **>(p), count * sizeof(T) + 16, s);
+}
+
+// RAII holder for temporaries of one call (freed stream-ordered).
+struct Temps {
+    cudaStream_t s;
+    void *p[32];
+    int k = 0;
+    explicit Temps(cudaStream_t st) : s(st) {}
+    template <typename T>
+    di_status get(T **out, size_t count)
+    {
+        if (k >= 32) return DI_ERR_OOM;
+        di_status r = dalloc_t(out, count, s);
+        if (r == DI_OK) p[k++] = *out;
+        return r;
+    }
+    ~Temps()
+    {
+        for (int i = 0; i < k; i++) dfree(p[i], s);
+    }
+};
+
+// ---------------------------------------------------------------- primitives
+// Exclusive prefix sum of n values (uint8/uint32/uint64 input) into uint64 out;
+// *total_dev receives the sum (device pointer, may be null).  Deterministic.
+template <typename T>
+di_status scan_exclusive(const T *in, uint64_t *out, int64_t n, uint64_t *total_dev,
+                         cudaStream_t s);
+
+// Stable LSD radix sort of (key, val) pairs over the listed bit ranges (each
+// range <= 8 bits, applied in order).  Result ends up in (*keys, *vals); the
+// alternate buffers are swapped in as needed.
+di_status radix_sort_pairs(uint64_t **keys, uint32_t **vals, uint64_t **keys_alt,
+                           uint32_t **vals_alt, int64_t n, const int *bit_lo,
+                           const int *bit_cnt, int npass, cudaStream_t s);
+
+// Bits needed to represent values in [0, n).
+inline int bits_for(int64_t n)
+{
+    int b = 0;
+    while (b < 63 && (int64_t(1) << b) < n) b++;
+    return b;
+}
+
+int sm_count(int device);
+
+// Kernel launches issued by the library (process-wide counter).
+void count_launches(int64_t k);
+int64_t launches();
+
+}  // namespace di
+
+// ---------------------------------------------------------------- handles
+struct di_graph_s {
+    int device = 0;
+    int64_t n = 0;
+    int64_t nnz = 0;
+    int64_t n_dangling = 0;
+    bool weighted = false;
+    bool off64 = false;       // reserved: offsets are uint32 (nnz < 2^32)
+    int64_t version = 0;      // bumped by every structural update
+    void *rp = nullptr;       // out-CSR row pointers, uint32 or uint64 [n+1]
+    int32_t *col = nullptr;   // targets [nnz]
+    double *w = nullptr;      // link weights [nnz] (weighted only)
+    double *wsum = nullptr;   // W_j = sum of row j's weights, left to right [n]
+    // in-link structure, built on demand
+    int64_t *cp = nullptr;    // [n+1]
+    int32_t *crow = nullptr;  // [nnz]
+    double *cw = nullptr;     // [nnz] (weighted only)
+};
+
+// Device-side control block of the sweep loop (one per state).
+struct DevCtl {
+    double theta;          // threshold used by the next selection
+    double l1;             // |F|_1 before the takes of the last selection
+    double stop_l1;        // (1 - d) tol
+    double d;
+    double theta_factor;
+    double final_l1;       // exact |F|_1 (final reduction)
+    double final_l;        // sum of H over dangling nodes (final reduction)
+    double pad0;
+    unsigned long long diffusions;
+    unsigned long long edge_pushes;
+    unsigned long long sweep;
+    unsigned long long max_sweeps;
+    unsigned long long total_edges;   // frontier links of the current sweep
+    unsigned long long total_entries; // frontier entries of the current sweep
+    unsigned long long maxbits;       // max |F_i| (IEEE bits) seen by the current selection
+    unsigned int nitems;       // push work items of the current sweep
+    unsigned int item_next;    // next push work item (dynamic queue)
+    unsigned int done;         // 0 running, 1 converged, 2 sweep cap
+    unsigned int ticket;       // last-block ticket of the selection
+    unsigned int ticket2;      // last-block ticket of the reductions
+    unsigned int err;
+};
+
+struct di_state_s {
+    di_graph_t g = nullptr;
+    int device = 0;
+    int64_t ntiles = 0;
+    int64_t max_items = 0;
+    double d = 0.85;
+    bool have_problem = false;
+    int64_t prep_version = 0;      // graph version the derived buffers were built for
+    int64_t problem_version = -1;  // graph version (H, F) belongs to
+    double *F = nullptr;
+    double *H = nullptr;
+    double *dscale = nullptr;      // d / W_j (or d / out(j)) per node, 0 if dangling
+    double dscale_d = -1.0;        // damping dscale was built for
+    // frontier (tile-sparse: tile t owns slots [t*TILE, t*TILE + cnt_t))
+    void *ent_row = nullptr;       // uint32/uint64 row start offset [ntiles*TILE]
+    void *ent_epos = nullptr;      // uint32/uint64 local link prefix [ntiles*TILE]
+    double *ent_val = nullptr;     // d F_i / W_i taken fluid share [ntiles*TILE]
+    unsigned int *tile_cnt = nullptr;
+    unsigned long long *tile_edges = nullptr;
+    unsigned int *tile_diff = nullptr;
+    double *tile_l1 = nullptr;
+    double *tile_l = nullptr;
+    unsigned int *item_tile = nullptr;
+    unsigned int *item_sub = nullptr;
+    DevCtl *ctl = nullptr;
+    DevCtl *host_ctl = nullptr;    // pinned mirror
+    // CUDA graph of the sweep loop
+    cudaGraphExec_t gexec = nullptr;
+    cudaStream_t gstream = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr, evp0 = nullptr, evp1 = nullptr;
+    // per-sweep frontier statistics (links, entries) written by the selection
+    unsigned long long *stats = nullptr;
+    cudaEvent_t *pev = nullptr;    // profile: event pairs around push launches
+    int npev = 0;
+};
+
+namespace di {
+constexpr int SEL_THREADS = 256;
+constexpr int SEL_PER_THREAD = 4;
+constexpr int TILE = SEL_THREADS * SEL_PER_THREAD;   // nodes per selection tile
+constexpr int PUSH_THREADS = 256;
+constexpr int PUSH_ITEM = 4096;                      // links per push work item
+constexpr int RED_THREADS = 256;
+constexpr int STAT_CAP = 4096;                       // sweeps with recorded statistics
+
+di_status graph_build_csc(di_graph_s *g, cudaStream_t s);
+di_status graph_create(int64_t n, int64_t nnz, const int64_t *ptr, const int32_t *idx, const void *w,
+                       int wdt, int layout, int mem, cudaStream_t s, di_graph_s *g);
+di_status graph_export(di_graph_s *g, bool csc, int64_t *ptr, int32_t *idx, double *w, int mem,
+                       cudaStream_t s);
+void graph_release(di_graph_s *g);
+int last_cuda();
+di_status copy_out_H(di_state_s *st, double *H_out, bool normalize, double l, int mem, cudaStream_t s);
+di_status state_l(di_graph_s *g, di_state_s *st, double *l, cudaStream_t s);
+di_status check_finite(const double *v, int64_t n, bool *ok, cudaStream_t s);
+di_status state_alloc(di_state_s *st, cudaStream_t s);
+di_status state_free(di_state_s *st);
+di_status solve_loop(di_graph_s *g, di_state_s *st, double tol, const di_opts *o, di_info *info,
+                     cudaStream_t s, bool fresh, const double *Z_dev);
+di_status l1_device(di_graph_s *g, const double *v, double *out_host, cudaStream_t s);
+di_status select_only(di_graph_s *g, const double *F, double theta, int32_t *ids, int64_t *count,
+                      cudaStream_t s);
+di_status update_edges(di_graph_s *g, di_state_s *st, int64_t m, const int32_t *src,
+                       const int32_t *dst, const double *w, const int8_t *op, cudaStream_t s);
+}  // namespace di

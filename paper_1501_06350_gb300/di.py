@@ -1,0 +1,226 @@
+"""Python face of libdi.so: graphs and solver states over torch CUDA tensors
+(device memory, streams) or NumPy arrays (host memory).
+
+Argument marshalling only; see include/di.h for the semantics of each call.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+_f64 = torch.float64
+
+
+def _is_dev(x) -> bool:
+    return isinstance(x, torch.Tensor) and x.is_cuda
+
+
+def _host(x, dtype):
+    if isinstance(x, torch.Tensor):
+        x = x.cpu().numpy()
+    return np.ascontiguousarray(x, dtype=dtype)
+
+
+def _stream(device=None):
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _p(x):
+    if x is None:
+        return None
+    if isinstance(x, torch.Tensor):
+        return ctypes.c_void_p(x.data_ptr())
+    return x.ctypes.data_as(ctypes.c_void_p)
+
+
+def _prep(x, dtype_np, dtype_t, mem):
+    """Input buffer for `mem`: contiguous cuda tensor or NumPy array."""
+    if x is None:
+        return None
+    if mem == L.DI_MEM_DEVICE:
+        if not _is_dev(x):
+            x = torch.as_tensor(np.asarray(x)).cuda()
+        return x.to(dtype_t).contiguous()
+    return _host(x, dtype_np)
+
+
+class Graph:
+    """Canonical diffusion structure of P (Section 2.1, Eq. def-p) on the GPU.
+
+    ``ptr``/``idx``/``w`` may be NumPy arrays (copied from host memory) or CUDA
+    tensors (read from device memory).  ``layout`` is "csr" (rows = sources)
+    or "csc" (rows = targets).  ``w`` may be float32 or float64.
+    """
+
+    def __init__(self, n: int, ptr, idx, w=None, layout: str = "csr"):
+        self._h = None
+        mem = L.DI_MEM_DEVICE if _is_dev(ptr) else L.DI_MEM_HOST
+        ptr = _prep(ptr, np.int64, torch.int64, mem)
+        idx = _prep(idx, np.int32, torch.int32, mem)
+        wdt = L.DI_W_NONE
+        if w is not None:
+            is32 = (w.dtype == torch.float32) if isinstance(w, torch.Tensor) else (np.asarray(w).dtype == np.float32)
+            wdt = L.DI_W_F32 if is32 else L.DI_W_F64
+            w = _prep(w, np.float32 if is32 else np.float64, torch.float32 if is32 else _f64, mem)
+        nnz = int(ptr[-1])
+        lay = {"csr": L.DI_LAYOUT_CSR, "csc": L.DI_LAYOUT_CSC}[layout]
+        h = ctypes.c_void_p()
+        L.check(L.lib().di_graph_create(n, nnz, _p(ptr), _p(idx), _p(w), wdt, lay, mem, _stream(),
+                                        ctypes.byref(h)), "di_graph_create")
+        self._h = h
+        self.n = n
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> dict:
+        n, nnz, nd = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        wt = ctypes.c_int()
+        L.check(L.lib().di_graph_info(self._h, ctypes.byref(n), ctypes.byref(nnz), ctypes.byref(nd),
+                                      ctypes.byref(wt)), "di_graph_info")
+        return dict(n=n.value, nnz=nnz.value, n_dangling=nd.value, weighted=bool(wt.value))
+
+    @property
+    def nnz(self) -> int:
+        return self.info()["nnz"]
+
+    def _export(self, fn, device: bool, weights: bool):
+        nnz = self.nnz
+        if device:
+            ptr = torch.empty(self.n + 1, dtype=torch.int64, device="cuda")
+            idx = torch.empty(max(nnz, 1), dtype=torch.int32, device="cuda")
+            w = torch.empty(max(nnz, 1), dtype=_f64, device="cuda") if weights else None
+            mem = L.DI_MEM_DEVICE
+        else:
+            ptr = np.empty(self.n + 1, dtype=np.int64)
+            idx = np.empty(max(nnz, 1), dtype=np.int32)
+            w = np.empty(max(nnz, 1), dtype=np.float64) if weights else None
+            mem = L.DI_MEM_HOST
+        L.check(fn(self._h, _p(ptr), _p(idx), _p(w), mem, _stream()), fn.__name__)
+        return ptr, idx[:nnz], (None if w is None else w[:nnz])
+
+    def export_csr(self, device: bool = False, weights: bool = True):
+        return self._export(L.lib().di_graph_export_csr, device, weights)
+
+    def export_csc(self, device: bool = False, weights: bool = True):
+        return self._export(L.lib().di_graph_export_csc, device, weights)
+
+    def close(self):
+        if self._h is not None and L._LIB is not None:
+            L.lib().di_graph_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _out_buffer(n, device: bool):
+    return torch.empty(n, dtype=_f64, device="cuda") if device else np.empty(n, dtype=np.float64)
+
+
+class State:
+    """Fluid F and history H of one problem on one graph (Section 3.1)."""
+
+    def __init__(self, graph: Graph):
+        self.graph = graph
+        h = ctypes.c_void_p()
+        L.check(L.lib().di_state_create(graph.handle, ctypes.byref(h)), "di_state_create")
+        self._h = h
+
+    def _finish(self, rc, where, info):
+        if rc not in (L.DI_OK, L.DI_ERR_NOT_CONVERGED):
+            raise L.DIError(rc, where)
+        out = info.as_dict()
+        out["converged"] = rc == L.DI_OK
+        return out
+
+    def solve(self, d: float = 0.85, Z=None, tol: float = 1e-9, out=None, device: bool = True, **opts):
+        """x = d P x + (1-d) Z from scratch; returns (H, info)."""
+        mem = L.DI_MEM_DEVICE if device else L.DI_MEM_HOST
+        Z = _prep(Z, np.float64, _f64, mem)
+        H = out if out is not None else _out_buffer(self.graph.n, device)
+        info = L.di_info()
+        o = L.default_opts(**opts)
+        rc = L.lib().di_solve(self.graph.handle, self._h, d, _p(Z), tol, ctypes.byref(o), _p(H),
+                              ctypes.byref(info), mem, _stream())
+        return H, self._finish(rc, "di_solve", info)
+
+    def resume(self, tol: float = 1e-9, out=None, device: bool = True, **opts):
+        mem = L.DI_MEM_DEVICE if device else L.DI_MEM_HOST
+        H = out if out is not None else _out_buffer(self.graph.n, device)
+        info = L.di_info()
+        o = L.default_opts(**opts)
+        rc = L.lib().di_resume(self.graph.handle, self._h, tol, ctypes.byref(o), _p(H),
+                               ctypes.byref(info), mem, _stream())
+        return H, self._finish(rc, "di_resume", info)
+
+    def update_edges(self, src, dst, op, w=None):
+        mem = L.DI_MEM_DEVICE if _is_dev(src) else L.DI_MEM_HOST
+        src = _prep(src, np.int32, torch.int32, mem)
+        dst = _prep(dst, np.int32, torch.int32, mem)
+        op = _prep(op, np.int8, torch.int8, mem)
+        w = _prep(w, np.float64, _f64, mem)
+        L.check(L.lib().di_update_edges(self.graph.handle, self._h, len(src), _p(src), _p(dst), _p(w),
+                                        _p(op), mem, _stream()), "di_update_edges")
+
+    def export(self, device: bool = False):
+        n = self.graph.n
+        H = _out_buffer(n, device)
+        F = _out_buffer(n, device)
+        l = ctypes.c_double()
+        L.check(L.lib().di_state_export(self._h, _p(H), _p(F), ctypes.byref(l),
+                                        L.DI_MEM_DEVICE if device else L.DI_MEM_HOST, _stream()),
+                "di_state_export")
+        return H, F, l.value
+
+    def import_state(self, H, F, d: float):
+        mem = L.DI_MEM_DEVICE if _is_dev(H) else L.DI_MEM_HOST
+        H = _prep(H, np.float64, _f64, mem)
+        F = _prep(F, np.float64, _f64, mem)
+        L.check(L.lib().di_state_import(self._h, _p(H), _p(F), d, mem, _stream()), "di_state_import")
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and L._LIB is not None:
+            L.lib().di_state_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def solve(graph: Graph, d: float = 0.85, Z=None, tol: float = 1e-9, **opts):
+    """One-shot solve; returns (H, info, state)."""
+    st = State(graph)
+    H, info = st.solve(d, Z, tol, **opts)
+    return H, info, st
+
+
+def frontier_select(graph: Graph, F, theta: float):
+    """Ascending ids with |F_i| >= theta, F_i != 0 (the solver's selection kernel)."""
+    mem = L.DI_MEM_DEVICE if _is_dev(F) else L.DI_MEM_HOST
+    F = _prep(F, np.float64, _f64, mem)
+    ids = torch.empty(graph.n, dtype=torch.int32, device="cuda") if mem else np.empty(graph.n, np.int32)
+    cnt = ctypes.c_int64()
+    L.check(L.lib().di_frontier_select(graph.handle, _p(F), theta, _p(ids), ctypes.byref(cnt), mem,
+                                       _stream()), "di_frontier_select")
+    return ids[:cnt.value]
+
+
+def residual_l1(graph: Graph, v) -> float:
+    mem = L.DI_MEM_DEVICE if _is_dev(v) else L.DI_MEM_HOST
+    v = _prep(v, np.float64, _f64, mem)
+    out = ctypes.c_double()
+    L.check(L.lib().di_residual_l1(graph.handle, _p(v), ctypes.byref(out), mem, _stream()),
+            "di_residual_l1")
+    return out.value

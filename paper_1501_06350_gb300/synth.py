@@ -25,7 +25,10 @@ is the solver's job (and the oracle's, independently).
 from __future__ import annotations
 
 import dataclasses
+import hashlib
+import json
 import math
+import os
 
 import numpy as np
 
@@ -318,3 +321,65 @@ def edge_batch(g_canon_ptr: np.ndarray, g_canon_idx: np.ndarray, n: int, frac: f
     op = np.concatenate([-np.ones(n_del, np.int8), np.ones(n_ins, np.int8)])
     perm = rng.permutation(len(src))
     return src[perm].astype(np.int32), dst[perm].astype(np.int32), op[perm]
+
+
+def cached(fn, **kw) -> RawGraph:
+    """Memoise a generator on disk (``$DI_SYNTH_CACHE``, default /tmp/di_synth_cache),
+    keyed by the generator name and its arguments."""
+    root = os.environ.get("DI_SYNTH_CACHE", "/tmp/di_synth_cache")
+    key = hashlib.sha1(json.dumps([fn.__name__, sorted(kw.items())], default=str).encode()).hexdigest()[:16]
+    path = os.path.join(root, f"{fn.__name__}_{key}.npz")
+    if os.path.exists(path):
+        z = np.load(path, allow_pickle=False)
+        meta = json.loads(str(z["meta"]))
+        return RawGraph(int(z["n"]), z["ptr"], z["idx"], z["w"] if "w" in z.files else None, meta)
+    g = fn(**kw)
+    os.makedirs(root, exist_ok=True)
+    tmp = path + f".tmp{os.getpid()}.npz"
+    arrs = dict(n=np.int64(g.n), ptr=g.ptr, idx=g.idx, meta=np.array(json.dumps(g.meta, default=str)))
+    if g.w is not None:
+        arrs["w"] = g.w
+    np.savez(tmp, **arrs)
+    os.replace(tmp, path)
+    return g
+
+
+def exact_batch(ptr: np.ndarray, idx: np.ndarray, n: int, frac: float, seed_offset: int):
+    """Link changes whose exact inverse is known: ``frac``/2 of the existing links
+    are deleted (distinct) and as many new distinct links (absent, no
+    self-link) are inserted.  Returns (src, dst, op) of the forward batch;
+    the inverse batch is the same pairs with op negated."""
+    rng = rng_for(5000 + seed_offset)
+    nnz = int(ptr[-1])
+    k = max(1, int(round(frac * nnz / 2)))
+    src_e = np.repeat(np.arange(n, dtype=np.int64), np.diff(ptr))
+    keys = src_e * n + idx.astype(np.int64)          # ascending for a canonical CSR
+    dpos = rng.choice(nnz, size=min(k, nnz), replace=False)
+    ds, dd = src_e[dpos], idx[dpos].astype(np.int64)
+    ins_s = np.zeros(0, np.int64)
+    ins_d = np.zeros(0, np.int64)
+    seen = set()
+    while len(ins_s) < k:
+        cs = rng.integers(0, n, size=2 * k)
+        cd = rng.integers(0, n, size=2 * k)
+        ck = cs * n + cd
+        pos = np.searchsorted(keys, ck)
+        exists = (pos < nnz) & (keys[np.minimum(pos, nnz - 1)] == ck) if nnz else np.zeros(len(ck), bool)
+        ok = (~exists) & (cs != cd)
+        _, first = np.unique(ck, return_index=True)
+        uniq = np.zeros(len(ck), bool)
+        uniq[first] = True
+        ok &= uniq
+        cand = [(a, b) for a, b in zip(cs[ok], cd[ok]) if (a * n + b) not in seen]
+        for a, b in cand:
+            seen.add(a * n + b)
+        if cand:
+            arr = np.array(cand, dtype=np.int64)
+            ins_s = np.concatenate([ins_s, arr[:, 0]])
+            ins_d = np.concatenate([ins_d, arr[:, 1]])
+    ins_s, ins_d = ins_s[:k], ins_d[:k]
+    src = np.concatenate([ds, ins_s]).astype(np.int32)
+    dst = np.concatenate([dd, ins_d]).astype(np.int32)
+    op = np.concatenate([-np.ones(len(ds), np.int8), np.ones(k, np.int8)])
+    perm = rng.permutation(len(src))
+    return src[perm], dst[perm], op[perm]

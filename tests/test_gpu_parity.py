@@ -1,0 +1,366 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Tolerances: index work (canonical CSR/CSC, frontier ids) is compared bit for
+bit; solutions are held to 1e-9 in L1 against the oracle's x (which is run to
+1e-13 or tighter), to 1e-6 relative per node when run to 1e-12, and to the
+certified bound |x - H|_1 <= |F|_1 / (1 - d) (Theorem 1, Eq. SL).  The fluid
+the GPU reports is checked against the exact residual (1-d) Z + d P H - H
+(Eq. HnFn) recomputed in FP64 on the CPU.
+"""
+import functools
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1501_06350_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+D = 0.85
+
+
+@pytest.fixture(scope="module")
+def di():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1501_06350_gb300 import build as b
+    b.build()
+    from paper_1501_06350_gb300 import di as m
+    return m
+
+
+@functools.lru_cache(maxsize=None)
+def pa10k():
+    return synth.pa_graph(n=10_000, m_target=100_000)
+
+
+@functools.lru_cache(maxsize=None)
+def canon(key):
+    g = GRAPHS[key]()
+    return oracle.canonical_csr(g.n, g.ptr, g.idx, g.w)
+
+
+@functools.lru_cache(maxsize=None)
+def web200k():
+    return synth.web_graph(n=200_000, m_target=2_000_000, seed_offset=12)
+
+
+@functools.lru_cache(maxsize=None)
+def web_w():
+    return synth.web_graph(n=30_000, m_target=300_000, weighted="lognormal32", seed_offset=14)
+
+
+GRAPHS = {"pa10k": pa10k, "web200k": web200k, "web_w": web_w}
+
+
+def _np(x):
+    return x.cpu().numpy() if hasattr(x, "cpu") else np.asarray(x)
+
+
+# ------------------------------------------------------------ A1: graph build
+@pytest.mark.parametrize("n,m,seed,weighted", [(1, 0, 0, False), (1, 3, 1, False), (7, 40, 2, True),
+                                               (1025, 9000, 3, False), (5000, 60000, 4, True),
+                                               (70001, 300001, 5, False)])
+@pytest.mark.parametrize("layout", ["csr", "csc"])
+def test_graph_build_bit_exact(di, n, m, seed, weighted, layout):
+    g = synth.small_graph(n, m, seed, dangling_frac=0.1, self_loops=True, weighted=weighted)
+    if layout == "csc":
+        g = synth.to_csc(g)
+    w32 = None if g.w is None else g.w.astype(np.float32)
+    G = di.Graph(g.n, g.ptr, g.idx, w32, layout=layout)
+    p, i, w = G.export_csr()
+    op, oi, ow = oracle.canonical_csr(g.n, g.ptr, g.idx, w32, 0 if layout == "csr" else 1)
+    assert np.array_equal(_np(p), op)
+    assert np.array_equal(_np(i), oi)
+    if weighted:
+        assert np.array_equal(_np(w), ow)
+    tp, ti, tw = G.export_csc()
+    qp, qi, qw = oracle.transpose(g.n, op, oi, ow)
+    assert np.array_equal(_np(tp), qp) and np.array_equal(_np(ti), qi)
+    if weighted:
+        assert np.array_equal(_np(tw), qw)
+    info = G.info()
+    assert info["nnz"] == len(oi) and info["n_dangling"] == int((np.diff(op) == 0).sum())
+
+
+def test_graph_build_from_device_buffers(di):
+    g = pa10k()
+    G = di.Graph(g.n, torch.from_numpy(g.ptr).cuda(), torch.from_numpy(g.idx).cuda())
+    p, i, _ = G.export_csr(device=True, weights=False)
+    cp, ci, _ = canon("pa10k")
+    assert np.array_equal(_np(p), cp) and np.array_equal(_np(i), ci)
+
+
+def test_graph_build_rejects_invalid(di):
+    from paper_1501_06350_gb300 import _lib as L
+    bad = [(np.array([0, 2, 1], np.int64), np.array([0, 1], np.int32), None),       # ptr[n] != nnz
+           (np.array([0, 2, 2], np.int64), np.array([0, 5], np.int32), None),       # idx out of range
+           (np.array([0, 1, 2], np.int64), np.array([0, 1], np.int32), np.array([1.0, -2.0])),
+           (np.array([0, 1, 2], np.int64), np.array([0, 1], np.int32), np.array([1.0, np.inf]))]
+    for ptr, idx, w in bad:
+        with pytest.raises(L.DIError) as e:
+            di.Graph(2, ptr, idx, w)
+        assert e.value.status in (L.DI_ERR_BAD_GRAPH, L.DI_ERR_INVALID_ARG)
+
+
+# ---------------------------------------------------------- A3: frontier ids
+@pytest.mark.parametrize("n", [1, 5, 1023, 1024, 1025, 4099, 100_003])
+def test_frontier_select_bit_exact(di, n):
+    g = synth.small_graph(n, 3 * n, 7, weighted=False)
+    G = di.Graph(g.n, g.ptr, g.idx)
+    rng = np.random.default_rng(n)
+    F = rng.standard_normal(n) * rng.random(n) ** 4
+    F[rng.random(n) < 0.2] = 0.0
+    F[rng.random(n) < 0.05] = -0.0
+    for theta in (0.0, np.abs(F).sum() / n, 0.5 * np.abs(F).sum() / n, float(np.abs(F).max()), 1e300):
+        ids = di.frontier_select(G, F, theta)
+        assert np.array_equal(_np(ids), oracle.select_frontier(F, theta))
+    # ties: |F_i| == theta is selected (DI-argmax takes "greater or equal")
+    F2 = np.full(n, 0.25)
+    assert len(di.frontier_select(G, torch.from_numpy(F2).cuda(), 0.25)) == n
+
+
+@pytest.mark.parametrize("n", [1, 1000, 1025, 250_001])
+def test_residual_l1_deterministic_and_accurate(di, n):
+    g = synth.small_graph(n, n, 3)
+    G = di.Graph(g.n, g.ptr, g.idx)
+    v = np.random.default_rng(1).standard_normal(n)
+    a = di.residual_l1(G, v)
+    b = di.residual_l1(G, torch.from_numpy(v).cuda())
+    exact = math.fsum(np.abs(v))
+    assert a == b
+    assert abs(a - exact) <= n * 2.3e-16 * exact
+
+
+# ------------------------------------------------------------ A2-A5: solve
+def _oracle_x(key, Z=None, tol=1e-13, d=D):
+    cp, ci, cw = canon(key)
+    g = GRAPHS[key]()
+    H, F, info, _ = oracle.di_solve(g.n, cp, ci, cw, d, Z, tol=tol)
+    return H, info
+
+
+@pytest.mark.parametrize("use_graph", [1, 0])
+def test_solve_matches_oracle_pa10k(di, use_graph):
+    g = pa10k()
+    G = di.Graph(g.n, g.ptr, g.idx)
+    tol = 1e-10 / (1 - D)           # |F|_1 <= 1e-10
+    H, info, st = di.solve(G, D, tol=tol, use_graph=use_graph)
+    x, oinfo = _oracle_x("pa10k")
+    Hn = _np(H)
+    err = np.abs(Hn - x).sum()
+    assert info["converged"] and info["resid_l1"] <= 1e-10
+    assert err <= 1e-9
+    assert err <= info["bound"] + oinfo["resid_l1"] / (1 - D) + 1e-13
+    # GPU fluid is the exact residual of its history (Eq. HnFn)
+    Hs, Fs, l = st.export()
+    cp, ci, _ = canon("pa10k")
+    r = oracle.residual(g.n, cp, ci, None, D, None, Hs)
+    assert np.abs(r - Fs).sum() < 1e-13
+    assert l == pytest.approx(oracle.dangling_loss(cp, Hs), rel=1e-12, abs=1e-300)
+    assert np.array_equal(Hs, Hn)
+
+
+def test_solve_per_node_relative(di):
+    g = pa10k()
+    G = di.Graph(g.n, g.ptr, g.idx)
+    H, info, _ = di.solve(G, D, tol=1e-12)
+    x, _ = _oracle_x("pa10k", tol=1e-14)
+    rel = np.abs(_np(H) - x) / x
+    assert rel.max() <= 1e-6
+
+
+@pytest.mark.parametrize("theta_factor", [0.05, 0.25, 0.5, 1.0])
+def test_solve_threshold_factors(di, theta_factor):
+    g = pa10k()
+    G = di.Graph(g.n, g.ptr, g.idx)
+    H, info, _ = di.solve(G, D, tol=1e-9, theta_factor=theta_factor)
+    x, _ = _oracle_x("pa10k")
+    assert info["converged"]
+    assert np.abs(_np(H) - x).sum() <= 1e-9
+
+
+@pytest.mark.parametrize("zkind", ["random", "signed", "seeds"])
+def test_solve_teleport_vectors(di, zkind):
+    g = web200k()
+    n = g.n
+    Z = {"random": lambda: synth.random_z(n, 1), "signed": lambda: synth.random_z(n, 2, signed=True),
+         "seeds": lambda: synth.seed_set_z(n, 500, 3)}[zkind]()
+    G = di.Graph(n, g.ptr, g.idx)
+    H, info, _ = di.solve(G, D, Z=Z, tol=1e-9)
+    x, _ = _oracle_x("web200k", Z=Z, tol=1e-12)
+    assert info["converged"]
+    assert np.abs(_np(H) - x).sum() <= 1e-9
+
+
+def test_solve_weighted(di):
+    g = web_w()
+    G = di.Graph(g.n, g.ptr, g.idx, g.w)
+    H, info, st = di.solve(G, D, tol=1e-10)
+    x, _ = _oracle_x("web_w", tol=1e-13)
+    assert np.abs(_np(H) - x).sum() <= 1e-9
+    cp, ci, cw = canon("web_w")
+    Hs, Fs, _ = st.export()
+    r = oracle.residual(g.n, cp, ci, cw, D, None, Hs)
+    assert np.abs(r - Fs).sum() < 1e-13
+
+
+def test_solve_normalised_matches_completed_matrix(di):
+    g = synth.small_graph(400, 1600, 11, dangling_frac=0.2)
+    G = di.Graph(g.n, g.ptr, g.idx)
+    cp, ci, _ = oracle.canonical_csr(g.n, g.ptr, g.idx)
+    Hn, info, _ = di.solve(G, D, tol=1e-11, normalize=1)
+    xc = oracle.completed_solution(g.n, cp, ci, None, D)
+    err = np.abs(_np(Hn) - xc).sum()
+    assert err <= info["bound_completed"] * (1 + 1e-9) + 1e-14
+    assert err < 1e-10
+
+
+@pytest.mark.parametrize("case", ["single", "single_loop", "all_dangling", "cycle", "complete"])
+def test_solve_degenerate_graphs(di, case):
+    if case == "single":
+        n, src, dst = 1, [], []
+    elif case == "single_loop":
+        n, src, dst = 1, [0], [0]
+    elif case == "all_dangling":
+        n, src, dst = 3000, [], []
+    elif case == "cycle":
+        n = 2051
+        src, dst = list(range(n)), [(i + 1) % n for i in range(n)]
+    else:
+        n = 40
+        src = [a for a in range(n) for b in range(n) if a != b]
+        dst = [b for a in range(n) for b in range(n) if a != b]
+    ptr = np.zeros(n + 1, np.int64)
+    np.add.at(ptr, np.array(src, dtype=np.int64) + 1, 1)
+    ptr = np.cumsum(ptr)
+    G = di.Graph(n, ptr, np.array(dst, np.int32))
+    H, info, _ = di.solve(G, D, tol=1e-12)
+    want = {"single": 1 - D, "single_loop": 1.0, "all_dangling": (1 - D) / n, "cycle": 1.0 / n,
+            "complete": 1.0 / n}[case]
+    assert info["converged"]
+    assert np.abs(_np(H) - want).sum() <= 1e-11
+
+
+def test_not_converged_status_keeps_state(di):
+    g = pa10k()
+    G = di.Graph(g.n, g.ptr, g.idx)
+    st = di.State(G)
+    H, info = st.solve(D, tol=1e-12, max_sweeps=3, use_graph=1)
+    assert not info["converged"] and info["sweeps"] == 3
+    Hs, Fs, _ = st.export()
+    assert np.array_equal(Hs, _np(H))
+    assert info["resid_l1"] == pytest.approx(math.fsum(np.abs(Fs)), rel=1e-12)
+    # resuming reaches the answer
+    H2, info2 = st.resume(tol=1e-10)
+    x, _ = _oracle_x("pa10k")
+    assert info2["converged"] and np.abs(_np(H2) - x).sum() <= 1e-9
+
+
+def test_invalid_arguments(di):
+    from paper_1501_06350_gb300 import _lib as L
+    g = pa10k()
+    G = di.Graph(g.n, g.ptr, g.idx)
+    st = di.State(G)
+    for kw in ({"d": 1.0}, {"d": 0.0}, {"tol": 0.0}, {"tol": float("nan")}):
+        args = dict(d=D, tol=1e-9)
+        args.update(kw)
+        with pytest.raises(L.DIError):
+            st.solve(**args)
+    Z = np.full(g.n, 1.0 / g.n)
+    Z[3] = np.nan
+    with pytest.raises(L.DIError):
+        st.solve(D, Z=Z)
+    for c in (-1.0, 0.0, 4.0, float("nan")):
+        with pytest.raises(L.DIError):
+            st.solve(D, theta_factor=c)
+
+
+def test_checkpoint_resume(di):
+    g = web200k()
+    G = di.Graph(g.n, g.ptr, g.idx)
+    a = di.State(G)
+    a.solve(D, tol=1e-4)
+    H, F, _ = a.export()
+    b = di.State(G)
+    b.import_state(H, F, D)
+    Hb, ib = b.resume(tol=1e-9)
+    x, _ = _oracle_x("web200k", tol=1e-12)
+    assert ib["converged"] and np.abs(_np(Hb) - x).sum() <= 1e-9
+
+
+# ------------------------------------------------------------- A6: update
+@pytest.mark.parametrize("key,frac,cut", [("pa10k", 0.01, None), ("pa10k", 0.2, 1e-3),
+                                          ("web_w", 0.01, None)])
+def test_update_matches_oracle(di, key, frac, cut):
+    g = GRAPHS[key]()
+    weighted = g.w is not None
+    G = di.Graph(g.n, g.ptr, g.idx, g.w)
+    st = di.State(G)
+    st.solve(D, tol=cut if cut else 1e-9)
+    H0, F0, _ = st.export()
+    cp, ci, cw = canon(key)
+    src, dst, op = synth.edge_batch(cp, ci, g.n, frac, 5)
+    wb = synth.rng_for(77).lognormal(size=len(src)) if weighted else None
+    st.update_edges(src, dst, op, wb)
+    # bit-exact new structure
+    p1, i1, w1 = G.export_csr()
+    qp, qi, qw = oracle.apply_batch(g.n, cp, ci, cw, src, dst, op, wb)
+    assert np.array_equal(_np(p1), qp) and np.array_equal(_np(i1), qi)
+    if weighted:
+        assert np.array_equal(_np(w1), qw)
+    # injected fluid F' = F + d (P' - P) H  (Theorem update)
+    H1, F1, _ = st.export()
+    assert np.array_equal(H1, H0)
+    Fo, changed = oracle.update_inject(g.n, (cp, ci, cw), (qp, qi, qw), D, H0, F0)
+    assert changed > 0
+    assert np.abs(F1 - Fo).sum() <= 1e-13
+    # resume converges to the solution of P'
+    H2, info = st.resume(tol=1e-10 / (1 - D))
+    Hx, Fx, oinfo, _ = oracle.di_solve(g.n, qp, qi, qw, D, tol=1e-13)
+    assert info["converged"] and np.abs(_np(H2) - Hx).sum() <= 1e-9
+
+
+def test_update_empty_batch_and_stale_state(di):
+    from paper_1501_06350_gb300 import _lib as L
+    g = pa10k()
+    G = di.Graph(g.n, g.ptr, g.idx)
+    a, b = di.State(G), di.State(G)
+    a.solve(D, tol=1e-9)
+    b.solve(D, tol=1e-9)
+    a.update_edges(np.zeros(0, np.int32), np.zeros(0, np.int32), np.zeros(0, np.int8))
+    cp, ci, _ = canon("pa10k")
+    p, i, _ = G.export_csr()
+    assert np.array_equal(_np(i), ci)
+    a.update_edges(np.array([0], np.int32), np.array([1], np.int32), np.array([1], np.int8))
+    with pytest.raises(L.DIError):         # b's (H, F) belong to the old matrix
+        b.resume(tol=1e-9)
+    H, info = b.solve(D, tol=1e-9)         # a fresh solve on P' is fine
+    assert info["converged"]
+
+
+# ------------------------------------------------------------- full size
+@functools.lru_cache(maxsize=None)
+def web4m():
+    return synth.cached(synth.web_graph, n=4_000_000, m_target=40_000_000)
+
+
+def test_full_size_web_graph(di):
+    """The 4M-page / 40M-link web graph in the benchmark's launch configuration
+    (CUDA-graph loop, theta factor 1, tol 1e-9): certified by the exact FP64
+    residual of the returned history and compared with the oracle's x."""
+    g = web4m()
+    G = di.Graph(g.n, g.ptr, g.idx)
+    st = di.State(G)
+    H, info = st.solve(D, tol=1e-9)
+    assert info["converged"]
+    Hs, Fs, _ = st.export()
+    cp, ci, _ = G.export_csr()
+    r = oracle.residual(g.n, cp, ci, None, D, None, Hs)
+    assert math.fsum(np.abs(r)) / (1 - D) <= 1e-9 * (1 + 1e-6)
+    assert np.abs(r - Fs).sum() <= 1e-12
+    x, _, oinfo, _ = oracle.di_solve(g.n, cp, ci, None, D, tol=1e-12)
+    assert np.abs(_np(H) - x).sum() <= 1e-9
