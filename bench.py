@@ -176,6 +176,10 @@ def main():
     ap.add_argument("--small", action="store_true", help="200k-page graph (quick check)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--theta", type=float, default=None,
+                    help="frontier threshold factor c (default: the library default)")
+    ap.add_argument("--eager", action="store_true",
+                    help="launch the sweep kernels one by one instead of the CUDA-graph loop")
     args = ap.parse_args()
     if args.warmup < 3 and not args.small:
         ap.error("--warmup must be >= 3")
@@ -209,12 +213,15 @@ def main():
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     L = _lib.lib()
 
+    ug = 0 if args.eager else 1
+    sopt = {} if args.theta is None else {"theta_factor": args.theta}
+
     def step():
-        H, i1 = st.solve(D, tol=TOL)
+        H, i1 = st.solve(D, tol=TOL, use_graph=ug, **sopt)
         st.update_edges(bs, bd, bo)
-        H, i2 = st.resume(tol=TOL)
+        H, i2 = st.resume(tol=TOL, use_graph=ug, **sopt)
         st.update_edges(bs, bd, bo_inv)
-        H, i3 = st.resume(tol=TOL)
+        H, i3 = st.resume(tol=TOL, use_graph=ug, **sopt)
         assert i1["converged"] and i2["converged"] and i3["converged"], (i1, i2, i3)
         return i1, i2, i3
 
@@ -235,12 +242,12 @@ def main():
     for k in range(args.steps):
         flush.zero_()
         ev[k][0].record()
-        _, i1 = st.solve(D, tol=TOL)
+        _, i1 = st.solve(D, tol=TOL, use_graph=ug, **sopt)
         ev[k][1].record()
         st.update_edges(bs, bd, bo)
-        _, i2 = st.resume(tol=TOL)
+        _, i2 = st.resume(tol=TOL, use_graph=ug, **sopt)
         st.update_edges(bs, bd, bo_inv)
-        _, i3 = st.resume(tol=TOL)
+        _, i3 = st.resume(tol=TOL, use_graph=ug, **sopt)
         ev[k][2].record()
         infos.append((i1, i2, i3))
     torch.cuda.synchronize()
@@ -263,7 +270,7 @@ def main():
     value = pushes_all / t_max
 
     # roofline of the dominant kernel (push), CUDA events around each launch
-    _, prof = st.solve(D, tol=TOL, profile=1)
+    _, prof = st.solve(D, tol=TOL, profile=1, **sopt)
     per_launch_links = prof["push_edges"] / max(prof["push_launches"], 1)
     push_avg_s = prof["push_ms"] / 1e3 / max(prof["push_launches"], 1)
     alg_bytes = 12.0 * per_launch_links

@@ -75,13 +75,16 @@ di_status prepare(di_graph_s *g, di_state_s *st, cudaStream_t s)
         st->gexec = nullptr;
     }
     st->dscale_d = -1.0;
-    const int64_t need = st->ntiles + g->nnz / PUSH_ITEM + 2;
+    const int64_t need = g->nnz / PIECE + g->nnz / HUB_DEG + 2;
     if (need > st->max_items) {
-        dfree(st->item_tile, s);
-        dfree(st->item_sub, s);
-        st->item_tile = st->item_sub = nullptr;
-        DI_TRY(dalloc_t(&st->item_tile, need, s));
-        DI_TRY(dalloc_t(&st->item_sub, need, s));
+        dfree(st->pc_row, s);
+        dfree(st->pc_len, s);
+        dfree(st->pc_val, s);
+        st->pc_row = st->pc_len = nullptr;
+        st->pc_val = nullptr;
+        DI_TRY(dalloc_t(&st->pc_row, need, s));
+        DI_TRY(dalloc_t(&st->pc_len, need, s));
+        DI_TRY(dalloc_t(&st->pc_val, need, s));
         st->max_items = need;
     }
     st->prep_version = g->version;

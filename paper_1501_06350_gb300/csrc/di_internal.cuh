@@ -111,29 +111,30 @@ struct DevCtl {
     double stop_l1;        // (1 - d) tol
     double d;
     double theta_factor;
-    double final_l1;       // exact |F|_1 (final reduction)
+    double final_l1;       // |F|_1 of the final state (FP64, fixed order)
     double final_l;        // sum of H over dangling nodes (final reduction)
     double pad0;
     unsigned long long diffusions;
     unsigned long long edge_pushes;
     unsigned long long sweep;
     unsigned long long max_sweeps;
-    unsigned long long total_edges;   // frontier links of the current sweep
-    unsigned long long total_entries; // frontier entries of the current sweep
-    unsigned long long maxbits;       // max |F_i| (IEEE bits) seen by the current selection
-    unsigned int nitems;       // push work items of the current sweep
-    unsigned int item_next;    // next push work item (dynamic queue)
+    unsigned long long total_edges;   // frontier links of the last selection
+    unsigned long long nent;          // dense frontier entries of the last selection
+    unsigned long long npieces;       // hub pieces being appended by the running selection
+    unsigned long long npieces_done;  // hub pieces of the last selection (read by the push)
+    int fx_shift;              // |F_i| are summed as integers in units of 2^-fx_shift
+    unsigned int tile_next;    // dynamic tile counter of the selection
     unsigned int done;         // 0 running, 1 converged, 2 sweep cap
     unsigned int ticket;       // last-block ticket of the selection
     unsigned int ticket2;      // last-block ticket of the reductions
-    unsigned int err;
+    unsigned int err;          // bit 0: a bounded wait of the selection gave up
 };
 
 struct di_state_s {
     di_graph_t g = nullptr;
     int device = 0;
     int64_t ntiles = 0;
-    int64_t max_items = 0;
+    int64_t max_items = 0;         // capacity of the hub-piece queue
     double d = 0.85;
     bool have_problem = false;
     int64_t prep_version = 0;      // graph version the derived buffers were built for
@@ -142,23 +143,30 @@ struct di_state_s {
     double *H = nullptr;
     double *dscale = nullptr;      // d / W_j (or d / out(j)) per node, 0 if dangling
     double dscale_d = -1.0;        // damping dscale was built for
-    // frontier (tile-sparse: tile t owns slots [t*TILE, t*TILE + cnt_t))
-    void *ent_row = nullptr;       // uint32/uint64 row start offset [ntiles*TILE]
-    void *ent_epos = nullptr;      // uint32/uint64 local link prefix [ntiles*TILE]
-    double *ent_val = nullptr;     // d F_i / W_i taken fluid share [ntiles*TILE]
+    // dense frontier of the last selection (ascending node order)
+    unsigned int *ent_row = nullptr;   // first link of the node's row
+    unsigned int *ent_deg = nullptr;   // out-degree (<= HUB_DEG)
+    double *ent_val = nullptr;         // d F_i / W_i: share pushed per unit weight
+    // hub pieces (rows longer than HUB_DEG, cut into PIECE links)
+    unsigned int *pc_row = nullptr;
+    unsigned int *pc_len = nullptr;
+    double *pc_val = nullptr;
+    // per-tile partials
     unsigned int *tile_cnt = nullptr;
     unsigned long long *tile_edges = nullptr;
     unsigned int *tile_diff = nullptr;
-    double *tile_l1 = nullptr;
+    unsigned long long *tile_fx = nullptr;   // |F|_1 fixed-point partial (lo, hi)
+    unsigned long long *tile_max = nullptr;
+    unsigned long long *lb_status = nullptr; // look-back words of the entry scan
+    unsigned int *lb_epoch = nullptr;        // selections run on this state (tags)
+    double *tile_l1 = nullptr;               // FP64 partials of the reductions
     double *tile_l = nullptr;
-    unsigned int *item_tile = nullptr;
-    unsigned int *item_sub = nullptr;
     DevCtl *ctl = nullptr;
     DevCtl *host_ctl = nullptr;    // pinned mirror
     // CUDA graph of the sweep loop
     cudaGraphExec_t gexec = nullptr;
     cudaStream_t gstream = nullptr;
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr, evp0 = nullptr, evp1 = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     // per-sweep frontier statistics (links, entries) written by the selection
     unsigned long long *stats = nullptr;
     cudaEvent_t *pev = nullptr;    // profile: event pairs around push launches
@@ -167,10 +175,11 @@ struct di_state_s {
 
 namespace di {
 constexpr int SEL_THREADS = 256;
-constexpr int SEL_PER_THREAD = 4;
+constexpr int SEL_PER_THREAD = 8;
 constexpr int TILE = SEL_THREADS * SEL_PER_THREAD;   // nodes per selection tile
 constexpr int PUSH_THREADS = 256;
-constexpr int PUSH_ITEM = 4096;                      // links per push work item
+constexpr int HUB_DEG = 256;                         // longer rows are pushed as pieces
+constexpr int PIECE = 1024;                          // links per hub piece
 constexpr int RED_THREADS = 256;
 constexpr int STAT_CAP = 4096;                       // sweeps with recorded statistics
 
