@@ -75,18 +75,7 @@ di_status prepare(di_graph_s *g, di_state_s *st, cudaStream_t s)
         st->gexec = nullptr;
     }
     st->dscale_d = -1.0;
-    const int64_t need = g->nnz / PIECE + g->nnz / HUB_DEG + 2;
-    if (need > st->max_items) {
-        dfree(st->pc_row, s);
-        dfree(st->pc_len, s);
-        dfree(st->pc_val, s);
-        st->pc_row = st->pc_len = nullptr;
-        st->pc_val = nullptr;
-        DI_TRY(dalloc_t(&st->pc_row, need, s));
-        DI_TRY(dalloc_t(&st->pc_len, need, s));
-        DI_TRY(dalloc_t(&st->pc_val, need, s));
-        st->max_items = need;
-    }
+    DI_TRY(state_prepare_graph(g, st, s));
     st->prep_version = g->version;
     return DI_OK;
 }

@@ -107,7 +107,7 @@ struct di_graph_s {
 // Device-side control block of the sweep loop (one per state).
 struct DevCtl {
     double theta;          // threshold used by the next selection
-    double l1;             // |F|_1 before the takes of the last selection
+    double l1;             // |F|_1 at the start of the last sweep
     double stop_l1;        // (1 - d) tol
     double d;
     double theta_factor;
@@ -116,18 +116,18 @@ struct DevCtl {
     double pad0;
     unsigned long long diffusions;
     unsigned long long edge_pushes;
-    unsigned long long sweep;
+    unsigned long long sweep;         // pushes performed by this call
     unsigned long long max_sweeps;
-    unsigned long long total_edges;   // frontier links of the last selection
-    unsigned long long nent;          // dense frontier entries of the last selection
-    unsigned long long npieces;       // hub pieces being appended by the running selection
-    unsigned long long npieces_done;  // hub pieces of the last selection (read by the push)
+    unsigned long long nhub;          // selected hub nodes appended by the running selection
+    unsigned long long npieces;       // hub pieces cut by the plan (read by the push)
+    unsigned long long sweep_links;   // links pushed by the running push
+    unsigned long long nent;          // frontier nodes of the last selection (mask bits)
     int fx_shift;              // |F_i| are summed as integers in units of 2^-fx_shift
-    unsigned int tile_next;    // dynamic tile counter of the selection
     unsigned int done;         // 0 running, 1 converged, 2 sweep cap
-    unsigned int ticket;       // last-block ticket of the selection
     unsigned int ticket2;      // last-block ticket of the reductions
-    unsigned int err;          // bit 0: a bounded wait of the selection gave up
+    unsigned int err;          // reserved for device-side error flags
+    unsigned int push_ready;   // 1: the mask/pieces describe a frontier not yet pushed
+    unsigned int pad1;
 };
 
 struct di_state_s {
@@ -143,22 +143,21 @@ struct di_state_s {
     double *H = nullptr;
     double *dscale = nullptr;      // d / W_j (or d / out(j)) per node, 0 if dangling
     double dscale_d = -1.0;        // damping dscale was built for
-    // dense frontier of the last selection (ascending node order)
-    unsigned int *ent_row = nullptr;   // first link of the node's row
-    unsigned int *ent_deg = nullptr;   // out-degree (<= HUB_DEG)
-    double *ent_val = nullptr;         // d F_i / W_i: share pushed per unit weight
+    // frontier of the last selection: one bit per selected node that is not a
+    // hub; selected hubs (more than HUB_DEG links) go to hub_list
+    unsigned int *mask = nullptr;      // [slots / 32]
+    unsigned int *hubbits = nullptr;   // [slots / 32] static: node has more than HUB_DEG links
+    unsigned int *hub_list = nullptr;  // [nhub_cap]
+    int64_t nhub_cap = 0;
     // hub pieces (rows longer than HUB_DEG, cut into PIECE links)
     unsigned int *pc_row = nullptr;
     unsigned int *pc_len = nullptr;
     double *pc_val = nullptr;
     // per-tile partials
     unsigned int *tile_cnt = nullptr;
-    unsigned long long *tile_edges = nullptr;
     unsigned int *tile_diff = nullptr;
     unsigned long long *tile_fx = nullptr;   // |F|_1 fixed-point partial (lo, hi)
     unsigned long long *tile_max = nullptr;
-    unsigned long long *lb_status = nullptr; // look-back words of the entry scan
-    unsigned int *lb_epoch = nullptr;        // selections run on this state (tags)
     double *tile_l1 = nullptr;               // FP64 partials of the reductions
     double *tile_l = nullptr;
     DevCtl *ctl = nullptr;
@@ -174,14 +173,15 @@ struct di_state_s {
 };
 
 namespace di {
-constexpr int SEL_THREADS = 256;
-constexpr int SEL_PER_THREAD = 8;
+constexpr int SEL_THREADS = 512;
+constexpr int SEL_PER_THREAD = 4;
 constexpr int TILE = SEL_THREADS * SEL_PER_THREAD;   // nodes per selection tile
 constexpr int PUSH_THREADS = 256;
 constexpr int HUB_DEG = 256;                         // longer rows are pushed as pieces
 constexpr int PIECE = 1024;                          // links per hub piece
 constexpr int RED_THREADS = 256;
 constexpr int STAT_CAP = 4096;                       // sweeps with recorded statistics
+constexpr int PLAN_CTAS = 32;                        // CTAs of the per-sweep plan kernel
 
 di_status graph_build_csc(di_graph_s *g, cudaStream_t s);
 di_status graph_create(int64_t n, int64_t nnz, const int64_t *ptr, const int32_t *idx, const void *w,
@@ -194,6 +194,7 @@ di_status copy_out_H(di_state_s *st, double *H_out, bool normalize, double l, in
 di_status state_l(di_graph_s *g, di_state_s *st, double *l, cudaStream_t s);
 di_status check_finite(const double *v, int64_t n, bool *ok, cudaStream_t s);
 di_status state_alloc(di_state_s *st, cudaStream_t s);
+di_status state_prepare_graph(di_graph_s *g, di_state_s *st, cudaStream_t s);
 di_status state_free(di_state_s *st);
 di_status solve_loop(di_graph_s *g, di_state_s *st, double tol, const di_opts *o, di_info *info,
                      cudaStream_t s, bool fresh, const double *Z_dev);

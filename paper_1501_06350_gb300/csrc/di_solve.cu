@@ -1,27 +1,27 @@
 // The D-Iteration sweep on the GPU (Section 3.1, Eq. defF; Section 3.4).
 //
-// One sweep diffuses a whole frontier S_t = { i : |F_i| >= theta_t } at once:
+// One sweep diffuses the frontier S_t = { i : |F_i| >= theta_t }:
 //
-//   select  (k_select)  one CTA per tile of TILE consecutive nodes (tile ids
-//           handed out in launch order).  Reads F, adds |F_i| to an exact
-//           fixed-point partial of |F|_1, applies the DI-argmax threshold,
-//           *takes* the fluid of the selected nodes (H_i += F_i, F_i = 0) and
-//           appends one frontier entry per selected node with out-links:
-//           rows of at most HUB_DEG links go to a dense, ascending entry
-//           array (tile offsets by a decoupled look-back scan), longer rows
-//           are cut into pieces of PIECE links on a separate queue.  The
-//           last CTA sums the tile partials (|F_t|_1, hence the next
-//           threshold and the stop test).
-//   push    (k_push)    warp-centric: a warp takes 32 consecutive entries,
-//           prefix-sums their degrees with shuffles, and walks their links
-//           32 at a time (coalesced reads of the link targets), adding
-//           d F_i P[k][i] to F_k with FP64 atomic adds; hub pieces are
-//           walked by one warp each.  No block barrier anywhere.
+//   select  (k_select)  streams F once: an exact fixed-point partial of
+//           |F_t|_1 and max |F_i| per tile, the DI-argmax test, and the
+//           frontier as a bit mask (one bit per node); selected hub rows
+//           (more than HUB_DEG links) go to a short list instead.
+//   plan    (k_plan)    every CTA sums the tile partials (integers, so all
+//           CTAs agree exactly), decides the stop test |F_t|_1/(1-d) <= tol
+//           (Theorem 1, Eq. SL) and the next threshold, and takes the fluid
+//           of the selected hubs (F is quiescent here), cutting their rows
+//           into pieces of PIECE links.
+//   push    (k_push)    warp-centric: a warp takes 32 nodes with their mask
+//           word, takes the fluid of the set ones with an atomic exchange,
+//           moves it into H, and scatters d F_i P[k][i] along their links with
+//           FP64 atomic adds; hub pieces are scattered the same way.  No block
+//           barrier inside the loop.
 //
-// Diffusing the set S_t at once keeps Eq. HnFn exact: with G = F restricted
-// to S_t, H' = H + G and F' = F - G + d P G, so H' + F' = F_0 + d P H'.  Every
-// selected node loses (1 - d) of its fluid (all of it if dangling), which is
-// the argument of Theorem 3.
+// Each atomic take-and-push is one elementary diffusion of Eq. defF (with
+// whatever fluid the node holds at that moment), so Eq. HnFn holds exactly
+// for any interleaving; every taken node loses (1 - d) of its fluid (all of it
+// if dangling), which is the argument of Theorem 3.  Nothing is taken before
+// the stop test, so the |F|_1 the test certifies is that of the final state.
 //
 // FP64 arithmetic is scarce on this part, so |F|_1 inside the sweep is summed
 // exactly as 128-bit integers (|F_i| rounded up to a multiple of 2^-fx_shift,
@@ -40,7 +40,6 @@ typedef unsigned __int128 u128;
 constexpr unsigned FULL = 0xffffffffu;
 constexpr unsigned long long ABS_MASK = 0x7fffffffffffffffull;
 constexpr int FX_TOP = 112;            // the initial |F|_1 is scaled below 2^FX_TOP
-constexpr unsigned SPIN_MAX = 1u << 22;
 
 __device__ __forceinline__ unsigned long long abs_bits(double x)
 {
@@ -68,29 +67,29 @@ __device__ __forceinline__ void red_add_f64(double *a, double v, unsigned long l
 {
     asm volatile("red.global.add.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(a), "d"(v), "l"(pol) : "memory");
 }
-__device__ __forceinline__ double2 ld_f64x2(const double *a, unsigned long long pol)
+// The cache-hinted loads and stores move raw 64-bit words: a double-typed
+// asm operand that is later reinterpreted as an integer costs an FP64
+// instruction per value on this part, and FP64 issue is scarce.
+__device__ __forceinline__ void ld_b64x2(const double *a, unsigned long long pol, unsigned long long &x,
+                                         unsigned long long &y)
 {
-    double2 r;
-    asm volatile("ld.global.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;"
-                 : "=d"(r.x), "=d"(r.y)
-                 : "l"(a), "l"(pol));
+    asm volatile("ld.global.L2::cache_hint.v2.b64 {%0, %1}, [%2], %3;" : "=l"(x), "=l"(y) : "l"(a), "l"(pol));
+}
+__device__ __forceinline__ unsigned long long ld_b64(const double *a, unsigned long long pol)
+{
+    unsigned long long r;
+    asm volatile("ld.global.L2::cache_hint.b64 %0, [%1], %2;" : "=l"(r) : "l"(a), "l"(pol));
     return r;
 }
-__device__ __forceinline__ double ld_f64(const double *a, unsigned long long pol)
+__device__ __forceinline__ void st_b64(double *a, unsigned long long v, unsigned long long pol)
 {
-    double r;
-    asm volatile("ld.global.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(r) : "l"(a), "l"(pol));
-    return r;
-}
-__device__ __forceinline__ void st_f64(double *a, double v, unsigned long long pol)
-{
-    asm volatile("st.global.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(a), "d"(v), "l"(pol) : "memory");
+    asm volatile("st.global.L2::cache_hint.b64 [%0], %1, %2;" ::"l"(a), "l"(v), "l"(pol) : "memory");
 }
 __device__ __forceinline__ double ldnc_f64(const double *a, unsigned long long pol)
 {
-    double r;
-    asm volatile("ld.global.nc.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(r) : "l"(a), "l"(pol));
-    return r;
+    unsigned long long r;
+    asm volatile("ld.global.nc.L2::cache_hint.b64 %0, [%1], %2;" : "=l"(r) : "l"(a), "l"(pol));
+    return __longlong_as_double((long long)r);
 }
 __device__ __forceinline__ unsigned ldnc_u32(const unsigned *a, unsigned long long pol)
 {
@@ -218,36 +217,35 @@ __global__ void k_scale(double *out, const double *in, int64_t n, double a)
         out[i] = a * in[i];
 }
 
-// Load the 8 fluid values of this thread with the F eviction priority.
-__device__ __forceinline__ void load8_keep(const double *F, int64_t i0, int64_t n, double f[8],
-                                          unsigned long long pol)
+// Load the IEEE bits of the P consecutive fluid values of this thread (0
+// past the end) with the eviction priority of F.
+template <int P>
+__device__ __forceinline__ void loadP_keep(const double *F, int64_t i0, int64_t n, unsigned long long *fb,
+                                           unsigned long long pol)
 {
-    if (i0 + 7 < n) {
+    if (i0 + P - 1 < n) {
 #pragma unroll
-        for (int q = 0; q < 4; q++) {
-            const double2 a = ld_f64x2(F + i0 + 2 * q, pol);
-            f[2 * q] = a.x;
-            f[2 * q + 1] = a.y;
-        }
+        for (int q = 0; q < P / 2; q++) ld_b64x2(F + i0 + 2 * q, pol, fb[2 * q], fb[2 * q + 1]);
     } else {
 #pragma unroll
-        for (int k = 0; k < 8; k++) f[k] = (i0 + k < n) ? ld_f64(F + i0 + k, pol) : 0.0;
+        for (int k = 0; k < P; k++) fb[k] = (i0 + k < n) ? ld_b64(F + i0 + k, pol) : 0ull;
     }
 }
 
-// Load the SEL_PER_THREAD (= 8) consecutive values of this thread (0 past the end).
-__device__ __forceinline__ void load8(const double *F, int64_t i0, int64_t n, double f[8])
+// Load the P consecutive values of this thread (0 past the end).
+template <int P>
+__device__ __forceinline__ void loadP(const double *F, int64_t i0, int64_t n, double *f)
 {
-    if (i0 + 7 < n) {
+    if (i0 + P - 1 < n) {
 #pragma unroll
-        for (int q = 0; q < 4; q++) {
+        for (int q = 0; q < P / 2; q++) {
             const double2 a = *reinterpret_cast<const double2 *>(F + i0 + 2 * q);
             f[2 * q] = a.x;
             f[2 * q + 1] = a.y;
         }
     } else {
 #pragma unroll
-        for (int k = 0; k < 8; k++) f[k] = (i0 + k < n) ? F[i0 + k] : 0.0;
+        for (int k = 0; k < P; k++) f[k] = (i0 + k < n) ? F[i0 + k] : 0.0;
     }
 }
 
@@ -266,15 +264,16 @@ __global__ void __launch_bounds__(SEL_THREADS) k_reduce(const double *v, const d
     __shared__ int s_last;
     const int64_t tile = blockIdx.x;
     const int64_t i0 = tile * TILE + (int64_t)threadIdx.x * SEL_PER_THREAD;
-    double f[8];
-    load8(v, i0, n, f);
+    constexpr int P = SEL_PER_THREAD;
+    double f[P];
+    loadP<P>(v, i0, n, f);
     double a = fabs(f[0]);
 #pragma unroll
-    for (int k = 1; k < 8; k++) a += fabs(f[k]);
+    for (int k = 1; k < P; k++) a += fabs(f[k]);
     double l = 0.0;
     if (H) {
 #pragma unroll
-        for (int k = 0; k < 8; k++) {
+        for (int k = 0; k < P; k++) {
             const int64_t i = i0 + k;
             if (i < n && rp[i + 1] == rp[i]) l += H[i];
         }
@@ -315,285 +314,288 @@ __global__ void __launch_bounds__(SEL_THREADS) k_reduce(const double *v, const d
 }
 
 // --------------------------------------------------------------- select
-// Per-thread counters packed for one block scan:
-//   bits 0..11 dense entries, 12..23 nodes taken, 24..63 links.
-constexpr int PK_TAKEN = 12;
-constexpr int PK_LINKS = 24;
-// look-back word: tag (24 bits) | flag (2 bits) | inclusive-or-local count (38 bits)
-constexpr unsigned long long LB_AGG = 1ull, LB_PRE = 2ull;
-
-__device__ __forceinline__ unsigned long long lb_word(unsigned tag, unsigned long long flag,
-                                                      unsigned long long v)
-{
-    return ((unsigned long long)(tag & 0xffffffu) << 40) | (flag << 38) | v;
-}
-
 __global__ void __launch_bounds__(SEL_THREADS)
-    k_select(const Off *__restrict__ rp, const double *__restrict__ dscale, double *F, double *H,
-             int64_t n, int64_t ntiles, Off *ent_row, Off *ent_deg, double *ent_val, Off *pc_row,
-             Off *pc_len, double *pc_val, unsigned *tile_cnt, unsigned long long *tile_edges,
-             unsigned *tile_diff, unsigned long long *tile_fx, unsigned long long *tile_max,
-             unsigned long long *lb_status, unsigned *lb_epoch, DevCtl *ctl, int use_cond,
-             cudaGraphConditionalHandle cond, int32_t *sel_ids, unsigned long long *stats)
+    k_select(const double *F, int64_t n, unsigned *mask, const unsigned *__restrict__ hubbits,
+             unsigned *hub_list, unsigned *tile_cnt, unsigned *tile_diff, unsigned long long *tile_fx,
+             unsigned long long *tile_max, DevCtl *ctl, int use_cond, cudaGraphConditionalHandle cond,
+             int32_t *sel_ids)
 {
-    __shared__ unsigned long long smu[SEL_THREADS / 32 + 1];
-    __shared__ unsigned long long s_fx[SEL_THREADS / 32][2];
-    __shared__ unsigned long long s_mx[SEL_THREADS / 32];
-    __shared__ unsigned long long s_base;
-    __shared__ unsigned s_tile;
-    __shared__ int s_last;
+    constexpr int P = SEL_PER_THREAD;
+    constexpr int NW = SEL_THREADS / 32;
+    static_assert(32 % P == 0, "a mask word must cover whole threads");
+    __shared__ unsigned long long s_fx[NW][2];
+    __shared__ unsigned long long s_mx[NW], s_cnt[NW];
+    __shared__ unsigned long long smu[NW + 1];
     volatile DevCtl *vc = ctl;
     if (vc->done) {
-        // Nothing left to do: the push that follows must find no work (its
-        // counts still describe the frontier it has already pushed), and a
+        // Nothing left to do: the push that follows must find no work, and a
         // graph while-loop must end here too.
         if (blockIdx.x == 0 && threadIdx.x == 0) {
-            vc->nent = 0;
-            vc->npieces_done = 0;
+            vc->push_ready = 0;
             if (use_cond) cudaGraphSetConditional(cond, 0u);
         }
         return;
     }
-    const double theta = vc->theta;
+    if (blockIdx.x == 0 && threadIdx.x == 0) vc->npieces = 0;   // the last push is over
+    const unsigned long long tb = abs_bits(vc->theta);
     const int fxs = vc->fx_shift;
-    const unsigned tag = *((volatile unsigned *)lb_epoch) + 1u;
-    const unsigned long long tb = abs_bits(theta);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x == 0) s_tile = atomicAdd(&ctl->tile_next, 1u);
-    __syncthreads();
-    const int64_t tile = s_tile;
-    const int64_t i0 = tile * TILE + (int64_t)threadIdx.x * SEL_PER_THREAD;
+    const int64_t tile = blockIdx.x;
+    const int64_t i0 = tile * TILE + (int64_t)threadIdx.x * P;
+    const unsigned long long keep = pol_last();
 
-    const unsigned long long keep = pol_last(), stream = pol_first();
-    double f[8];
-    load8_keep(F, i0, n, f, keep);
+    unsigned long long fb[P];
+    loadP_keep<P>(F, i0, n, fb, keep);
+    const unsigned hubw = (__ldg(hubbits + i0 / 32) >> (i0 % 32)) & ((1u << P) - 1u);
     u128 fx = 0;
     unsigned selm = 0;
     unsigned long long mb = 0;
 #pragma unroll
-    for (int k = 0; k < 8; k++) {
-        const unsigned long long b = abs_bits(f[k]);
+    for (int k = 0; k < P; k++) {
+        const unsigned long long b = fb[k] & ABS_MASK;
         fx += to_fixed(b, fxs);
         if ((i0 + k < n) && b != 0 && b >= tb) selm |= 1u << k;
         mb = b > mb ? b : mb;
     }
-    Off r[9];
-    unsigned long long packed = (unsigned long long)__popc(selm) << PK_TAKEN;
-    unsigned npc = 0;
-    if (selm) {
+    const unsigned bits = selm & ~hubw;   // taken by the push
+    const unsigned hubs = selm & hubw;    // taken by the plan
+    // selected hubs: one list reservation per warp
+    {
+        const unsigned nh = __popc(hubs);
+        unsigned incl = nh;
 #pragma unroll
-        for (int k = 0; k < 9; k++) r[k] = (i0 + k <= n) ? ldnc_u32(rp + i0 + k, stream) : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const unsigned wtot = __shfl_sync(FULL, incl, 31);
+        if (wtot) {
+            unsigned long long wbase = 0;
+            if (lane == 31) wbase = atomicAdd((unsigned long long *)&ctl->nhub, (unsigned long long)wtot);
+            wbase = __shfl_sync(FULL, wbase, 31);
+            unsigned long long pb = wbase + incl - nh;
 #pragma unroll
-        for (int k = 0; k < 8; k++) {
-            const Off deg = r[k + 1] - r[k];
-            if (!((selm >> k) & 1u) || deg == 0) continue;
-            packed += (unsigned long long)deg << PK_LINKS;
-            if (deg <= (Off)HUB_DEG) packed += 1ull;
-            else npc += (deg + PIECE - 1) / PIECE;
+            for (int k = 0; k < P; k++)
+                if ((hubs >> k) & 1u) hub_list[pb++] = (unsigned)(i0 + k);
         }
     }
-    // warp partials of |F|_1 (exact integers) and of max |F_i|
+    // mask word of 32 consecutive nodes = OR over 32 / P threads
+    {
+        unsigned word = bits << (P * (lane % (32 / P)));
+#pragma unroll
+        for (int o = 1; o < 32 / P; o <<= 1) word |= __shfl_xor_sync(FULL, word, o);
+        if (lane % (32 / P) == 0) mask[i0 / 32] = word;
+    }
+    // verification output: ascending ids of the selected nodes inside the tile
+    if (sel_ids) {
+        unsigned long long tot;
+        unsigned long long spos = block_exscan_u64<SEL_THREADS>((unsigned long long)__popc(selm), smu, &tot);
+#pragma unroll
+        for (int k = 0; k < P; k++)
+            if ((selm >> k) & 1u) sel_ids[tile * TILE + (int64_t)(spos++)] = (int32_t)(i0 + k);
+    }
+    // tile partials (integers, hence exact in any order)
+    unsigned long long cnt = (unsigned long long)__popc(bits) | ((unsigned long long)__popc(selm) << 32);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         fx += shfl_xor_u128(fx, o);
         const unsigned long long y = __shfl_xor_sync(FULL, mb, o);
         mb = y > mb ? y : mb;
+        cnt += __shfl_xor_sync(FULL, cnt, o);
     }
     if (lane == 0) {
         s_fx[warp][0] = (unsigned long long)fx;
         s_fx[warp][1] = (unsigned long long)(fx >> 64);
         s_mx[warp] = mb;
-    }
-    unsigned long long tot;
-    const unsigned long long pre = block_exscan_u64<SEL_THREADS>(packed, smu, &tot);
-    const unsigned long long cnt = tot & 0xfff;
-
-    // tile offset in the dense entry array: decoupled look-back over the
-    // tiles handed out before this one (they are all running or done)
-    if (threadIdx.x == 0) {
-        unsigned long long base = 0;
-        if (tile == 0) {
-            atomicExch(lb_status, lb_word(tag, LB_PRE, cnt));
-        } else {
-            atomicExch(lb_status + tile, lb_word(tag, LB_AGG, cnt));
-            for (int64_t p = tile - 1; p >= 0; p--) {
-                unsigned long long wv = 0;
-                unsigned it = 0;
-                for (; it < SPIN_MAX; it++) {
-                    wv = *((volatile unsigned long long *)(lb_status + p));
-                    if ((unsigned)(wv >> 40) == (tag & 0xffffffu) && ((wv >> 38) & 3ull)) break;
-                    __nanosleep(64);
-                }
-                if (it == SPIN_MAX) {          // give up: flag the error, keep positions in range
-                    atomicOr(&ctl->err, 1u);
-                    break;
-                }
-                base += wv & ((1ull << 38) - 1);
-                if (((wv >> 38) & 3ull) == LB_PRE) break;
-            }
-            atomicExch(lb_status + tile, lb_word(tag, LB_PRE, base + cnt));
-        }
-        s_base = base;
+        s_cnt[warp] = cnt;
     }
     __syncthreads();
-    if (selm) {
-        unsigned long long pos = s_base + (pre & 0xfff);
-        unsigned spos = (unsigned)((pre >> PK_TAKEN) & 0xfff);
-        const int64_t slot0 = tile * TILE;
-        unsigned pbase = npc ? (unsigned)atomicAdd(&ctl->npieces, (unsigned long long)npc) : 0u;
-#pragma unroll
-        for (int k = 0; k < 8; k++) {
-            if (!((selm >> k) & 1u)) continue;
-            const int64_t i = i0 + k;
-            st_f64(H + i, ld_f64(H + i, stream) + f[k], stream);
-            st_f64(F + i, 0.0, keep);
-            if (sel_ids) sel_ids[slot0 + spos++] = (int32_t)i;
-            const Off deg = r[k + 1] - r[k];
-            if (deg == 0) continue;
-            const double v = f[k] * ldnc_f64(dscale + i, stream);
-            if (deg <= (Off)HUB_DEG) {
-                ent_row[pos] = r[k];
-                ent_deg[pos] = deg;
-                ent_val[pos] = v;
-                pos++;
-            } else {
-                for (Off o = 0; o < deg; o += PIECE) {
-                    pc_row[pbase] = r[k] + o;
-                    pc_len[pbase] = deg - o < (Off)PIECE ? deg - o : (Off)PIECE;
-                    pc_val[pbase] = v;
-                    pbase++;
-                }
-            }
-        }
-    }
     if (threadIdx.x == 0) {
         u128 t = 0;
-        unsigned long long mx = 0;
+        unsigned long long mx = 0, c = 0;
 #pragma unroll
-        for (int w = 0; w < SEL_THREADS / 32; w++) {
+        for (int w = 0; w < NW; w++) {
             t += ((u128)s_fx[w][1] << 64) | s_fx[w][0];
             mx = s_mx[w] > mx ? s_mx[w] : mx;
+            c += s_cnt[w];
         }
         tile_fx[2 * tile] = (unsigned long long)t;
         tile_fx[2 * tile + 1] = (unsigned long long)(t >> 64);
         tile_max[tile] = mx;
-        tile_cnt[tile] = (unsigned)cnt;
-        tile_edges[tile] = tot >> PK_LINKS;
-        tile_diff[tile] = (unsigned)((tot >> PK_TAKEN) & 0xfff);
-        __threadfence();
-        const unsigned tk = atomicAdd(&ctl->ticket, 1u);
-        s_last = (tk == (unsigned)(ntiles - 1));
+        tile_cnt[tile] = (unsigned)(c & 0xffffffffu);
+        tile_diff[tile] = (unsigned)(c >> 32);
     }
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
+}
 
-    // ---- epilogue: one CTA; integer totals are order-free, hence exact
+// ----------------------------------------------------------------- plan
+// Every CTA sums the tile partials; CTA 0 updates the control block.  Then
+// the selected hubs are taken (F is not being written by anyone here) and
+// their rows cut into pieces for the push.
+__global__ void __launch_bounds__(SEL_THREADS)
+    k_plan(double *F, double *H, const Off *__restrict__ rp, const double *__restrict__ dscale, int64_t n,
+           int64_t ntiles, const unsigned *__restrict__ hub_list, Off *pc_row, Off *pc_len, double *pc_val,
+           const unsigned *tile_cnt, const unsigned *tile_diff, const unsigned long long *tile_fx,
+           const unsigned long long *tile_max, DevCtl *ctl, int use_cond, cudaGraphConditionalHandle cond,
+           unsigned long long *stats)
+{
+    constexpr int NW = SEL_THREADS / 32;
+    __shared__ unsigned long long s_red[5][NW];
+    __shared__ unsigned s_go;
+    volatile DevCtl *vc = ctl;
+    if (vc->done) return;   // the selection has already closed the loop
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     u128 sfx = 0;
-    unsigned long long sd = 0, se = 0, sc = 0, mx = 0;
+    unsigned long long sd = 0, sc = 0, mx = 0;
 #pragma unroll 4
     for (int64_t k = threadIdx.x; k < ntiles; k += SEL_THREADS) {
-        sfx += ((u128)__ldcg(tile_fx + 2 * k + 1) << 64) | __ldcg(tile_fx + 2 * k);
-        sd += __ldcg(tile_diff + k);
-        se += __ldcg(tile_edges + k);
-        sc += __ldcg(tile_cnt + k);
-        const unsigned long long m = __ldcg(tile_max + k);
+        sfx += ((u128)__ldg(tile_fx + 2 * k + 1) << 64) | __ldg(tile_fx + 2 * k);
+        sd += __ldg(tile_diff + k);
+        sc += __ldg(tile_cnt + k);
+        const unsigned long long m = __ldg(tile_max + k);
         mx = m > mx ? m : mx;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         sfx += shfl_xor_u128(sfx, o);
         sd += __shfl_xor_sync(FULL, sd, o);
-        se += __shfl_xor_sync(FULL, se, o);
         sc += __shfl_xor_sync(FULL, sc, o);
         const unsigned long long y = __shfl_xor_sync(FULL, mx, o);
         mx = y > mx ? y : mx;
     }
-    __shared__ unsigned long long s_red[6][SEL_THREADS / 32];
     if (lane == 0) {
         s_red[0][warp] = (unsigned long long)sfx;
         s_red[1][warp] = (unsigned long long)(sfx >> 64);
         s_red[2][warp] = sd;
-        s_red[3][warp] = se;
-        s_red[4][warp] = sc;
-        s_red[5][warp] = mx;
+        s_red[3][warp] = sc;
+        s_red[4][warp] = mx;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         sfx = 0;
-        sd = se = sc = mx = 0;
-        for (int w = 0; w < SEL_THREADS / 32; w++) {
+        sd = sc = mx = 0;
+        for (int w = 0; w < NW; w++) {
             sfx += ((u128)s_red[1][w] << 64) | s_red[0][w];
             sd += s_red[2][w];
-            se += s_red[3][w];
-            sc += s_red[4][w];
-            mx = s_red[5][w] > mx ? s_red[5][w] : mx;
+            sc += s_red[3][w];
+            mx = s_red[4][w] > mx ? s_red[4][w] : mx;
         }
-        const double sa = from_fixed(sfx, fxs);
-        ctl->l1 = sa;
-        ctl->nent = sc;
-        ctl->npieces_done = *((volatile unsigned long long *)&ctl->npieces);
-        ctl->npieces = 0;
-        ctl->total_edges = se;
-        ctl->diffusions += sd;
-        ctl->edge_pushes += se;
-        const unsigned long long sweep = ctl->sweep + 1;
-        ctl->sweep = sweep;
-        if (stats && sweep <= (unsigned long long)STAT_CAP) {
-            stats[2 * (sweep - 1)] = se;
-            stats[2 * (sweep - 1) + 1] = sc;
-        }
+        const double sa = from_fixed(sfx, vc->fx_shift);
+        const unsigned long long sweep = vc->sweep;
         unsigned done = 0;
         // the integer sum rounds every |F_i| up, so it bounds |F_t|_1 from above
-        if (sa <= ctl->stop_l1) done = 1;
-        else if (sweep >= ctl->max_sweeps) done = 2;
-        if (ctl->err) done = 3;
-        double th = ctl->theta_factor * sa / (double)n;
-        // A sweep that took nothing left F unchanged; the largest |F_i| passes
-        // the DI-argmax test exactly, so never ask for more than that (this
-        // covers a rounded average above every one of several equal fluids).
-        const double fmax = __longlong_as_double((long long)mx);
-        if (sd == 0 && fmax < th) th = fmax;
-        ctl->theta = th;
-        ctl->ticket = 0;
-        ctl->tile_next = 0;
-        *lb_epoch = tag;
-        __threadfence();
-        ctl->done = done;
-        if (use_cond) cudaGraphSetConditional(cond, done ? 0u : 1u);
+        if (sa <= vc->stop_l1) done = 1;
+        else if (sweep >= vc->max_sweeps) done = 2;
+        s_go = done == 0;
+        if (blockIdx.x == 0) {
+            // fold the links of the previous push into the totals
+            const unsigned long long links = vc->sweep_links;
+            vc->edge_pushes = vc->edge_pushes + links;
+            if (stats && sweep >= 1 && sweep <= (unsigned long long)STAT_CAP) stats[2 * (sweep - 1)] = links;
+            vc->sweep_links = 0;
+            vc->l1 = sa;
+            if (!done) {
+                vc->diffusions = vc->diffusions + sd;
+                vc->nent = sc;
+                if (stats && sweep < (unsigned long long)STAT_CAP) stats[2 * sweep + 1] = sc;
+                double th = vc->theta_factor * sa / (double)n;
+                // A sweep that took nothing leaves F unchanged; the largest |F_i|
+                // passes the DI-argmax test exactly, so never ask for more than
+                // that (this covers a rounded average above several equal fluids).
+                const double fmax = __longlong_as_double((long long)mx);
+                if (sd == 0 && fmax < th) th = fmax;
+                vc->theta = th;
+            }
+            vc->push_ready = done ? 0u : 1u;
+            __threadfence();
+            vc->done = done;
+            if (use_cond) cudaGraphSetConditional(cond, done ? 0u : 1u);
+        }
+    }
+    __syncthreads();
+    if (!s_go) return;
+    // take the selected hubs: one thread each
+    const unsigned long long nhub = vc->nhub;
+    const unsigned long long stream = pol_first(), keep = pol_last();
+    for (unsigned long long h = (unsigned long long)blockIdx.x * SEL_THREADS + threadIdx.x; h < nhub;
+         h += (unsigned long long)gridDim.x * SEL_THREADS) {
+        const unsigned i = hub_list[h];
+        const unsigned long long fbits = ld_b64(F + i, keep);
+        const Off r0 = ldnc_u32(rp + i, stream), r1 = ldnc_u32(rp + i + 1, stream);
+        const unsigned long long hb = ld_b64(H + i, stream);
+        const double ds = ldnc_f64(dscale + i, stream);
+        const double f = __longlong_as_double((long long)fbits);
+        st_b64(H + i, (unsigned long long)__double_as_longlong(__longlong_as_double((long long)hb) + f), stream);
+        st_b64(F + i, 0ull, keep);
+        const Off deg = r1 - r0;
+        const double v = f * ds;
+        const unsigned np = (deg + PIECE - 1) / PIECE;
+        unsigned long long pb = atomicAdd((unsigned long long *)&ctl->npieces, (unsigned long long)np);
+        for (Off o = 0; o < deg; o += PIECE) {
+            pc_row[pb] = r0 + o;
+            pc_len[pb] = deg - o < (Off)PIECE ? deg - o : (Off)PIECE;
+            pc_val[pb] = v;
+            pb++;
+        }
     }
 }
 
 // ----------------------------------------------------------------- push
-// Warp-centric push.  Work unit u < nchunks: entries [32u, 32u + 32) of the
-// dense frontier; u >= nchunks: hub piece u - nchunks.  Lane j of a chunk
-// owns entry 32u + j; the chunk's links are enumerated 32 at a time and each
-// lane finds the entry of its link by a binary search over the lanes'
-// exclusive degree prefixes (shuffles only).
+__device__ __forceinline__ unsigned long long atom_exch_b64(double *a, unsigned long long v,
+                                                            unsigned long long pol)
+{
+    unsigned long long old;
+    asm volatile("atom.global.exch.L2::cache_hint.b64 %0, [%1], %2, %3;"
+                 : "=l"(old)
+                 : "l"(a), "l"(v), "l"(pol)
+                 : "memory");
+    return old;
+}
+
+// Warp-centric take and push.  Work unit u < ngroups: the 32 nodes
+// [32u, 32u + 32) and their mask word; u >= ngroups: hub piece u - ngroups.
+// The links of the taken nodes are enumerated 32 at a time and each lane
+// finds the node of its link by a binary search over the lanes' exclusive
+// degree prefixes (shuffles only).
 template <bool WEIGHTED>
 __global__ void __launch_bounds__(PUSH_THREADS)
-    k_push(const Off *__restrict__ ent_row, const Off *__restrict__ ent_deg,
-           const double *__restrict__ ent_val, const Off *__restrict__ pc_row,
-           const Off *__restrict__ pc_len, const double *__restrict__ pc_val,
-           const int32_t *__restrict__ col, const double *__restrict__ w, double *F, const DevCtl *ctl)
+    k_push(double *F, double *H, const Off *__restrict__ rp, const double *__restrict__ dscale,
+           const unsigned *__restrict__ mask, const Off *__restrict__ pc_row, const Off *__restrict__ pc_len,
+           const double *__restrict__ pc_val, int64_t ngroups, const int32_t *__restrict__ col,
+           const double *__restrict__ w, DevCtl *ctl)
 {
-    const unsigned long long nent = ((volatile const DevCtl *)ctl)->nent;
-    const unsigned long long npc = ((volatile const DevCtl *)ctl)->npieces_done;
+    __shared__ unsigned long long s_links[PUSH_THREADS / 32];
+    volatile DevCtl *vc = ctl;
+    if (!vc->push_ready) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        vc->nhub = 0;                 // the plan has consumed the hub list
+        vc->sweep = vc->sweep + 1;    // (the plan reads it; it is stable until here)
+    }
+    const unsigned long long npc = vc->npieces;
     const unsigned long long keep = pol_last(), stream = pol_first();
     const int lane = threadIdx.x & 31;
-    const unsigned long long nchunks = (nent + 31) / 32;
-    const unsigned long long nunits = nchunks + npc;
+    const unsigned long long nunits = (unsigned long long)ngroups + npc;
     const unsigned long long wid = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const unsigned long long nw = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
+    unsigned long long links = 0;
     for (unsigned long long u = wid; u < nunits; u += nw) {
-        if (u < nchunks) {
-            const unsigned long long k = u * 32 + lane;
+        if (u < (unsigned long long)ngroups) {
+            const unsigned m = ldnc_u32(mask + u, stream);
+            if (m == 0) continue;
+            const unsigned long long i = u * 32 + lane;
             Off row = 0, deg = 0;
-            double val = 0.0;
-            if (k < nent) {
-                row = ldnc_u32(ent_row + k, stream);
-                deg = ldnc_u32(ent_deg + k, stream);
-                val = ldnc_f64(ent_val + k, stream);
+            double v0 = 0.0;
+            if ((m >> lane) & 1u) {
+                // take (Eq. defF): whatever fluid node i holds now, into H(i)
+                const unsigned long long fbits = atom_exch_b64(F + i, 0ull, keep);
+                row = ldnc_u32(rp + i, stream);
+                const Off r1 = ldnc_u32(rp + i + 1, stream);
+                const unsigned long long hb = ld_b64(H + i, stream);
+                const double ds = ldnc_f64(dscale + i, stream);
+                const double f = __longlong_as_double((long long)fbits);
+                st_b64(H + i, (unsigned long long)__double_as_longlong(__longlong_as_double((long long)hb) + f),
+                       stream);
+                deg = r1 - row;
+                v0 = f * ds;
             }
             Off incl = deg;
 #pragma unroll
@@ -603,6 +605,7 @@ __global__ void __launch_bounds__(PUSH_THREADS)
             }
             const Off total = __shfl_sync(FULL, incl, 31);
             const Off excl = incl - deg;
+            links += total;
             // lanes' links are e = base + lane; four groups in flight
             for (Off base = 0; base < total; base += 128) {
                 int32_t c[4];
@@ -619,7 +622,7 @@ __global__ void __launch_bounds__(PUSH_THREADS)
                     }
                     const Off rj = __shfl_sync(FULL, row, j);
                     const Off xj = __shfl_sync(FULL, excl, j);
-                    const double vj = __shfl_sync(FULL, val, j);
+                    const double vj = __shfl_sync(FULL, v0, j);
                     c[g] = -1;
                     v[g] = vj;
                     if (e < total) {
@@ -633,9 +636,10 @@ __global__ void __launch_bounds__(PUSH_THREADS)
                     if (c[g] >= 0) red_add_f64(F + c[g], v[g], keep);
             }
         } else {
-            const unsigned long long p = u - nchunks;
+            const unsigned long long p = u - (unsigned long long)ngroups;
             const Off row = ldnc_u32(pc_row + p, stream), len = ldnc_u32(pc_len + p, stream);
-            const double val = ldnc_f64(pc_val + p, stream);
+            const double pv = ldnc_f64(pc_val + p, stream);
+            links += len;
             for (Off base = 0; base < len; base += 128) {
                 int32_t c[4];
                 double v[4];
@@ -643,10 +647,10 @@ __global__ void __launch_bounds__(PUSH_THREADS)
                 for (int g = 0; g < 4; g++) {
                     const Off e = base + (Off)(g * 32 + lane);
                     c[g] = -1;
-                    v[g] = val;
+                    v[g] = pv;
                     if (e < len) {
                         c[g] = ldnc_s32(col + row + e, stream);
-                        if (WEIGHTED) v[g] = val * ldnc_f64(w + row + e, stream);
+                        if (WEIGHTED) v[g] = pv * ldnc_f64(w + row + e, stream);
                     }
                 }
 #pragma unroll
@@ -655,6 +659,31 @@ __global__ void __launch_bounds__(PUSH_THREADS)
             }
         }
     }
+    if (lane == 0) s_links[threadIdx.x >> 5] = links;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int q = 0; q < PUSH_THREADS / 32; q++) t += s_links[q];
+        if (t) atomicAdd((unsigned long long *)&ctl->sweep_links, t);
+    }
+}
+
+// Static hub bit mask: node i has more than HUB_DEG out-links.
+__global__ void k_hubbits(const Off *rp, int64_t n, int64_t words, unsigned *hubbits,
+                          unsigned long long *count)
+{
+    unsigned long long c = 0;
+    for (int64_t wi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; wi < words;
+         wi += (int64_t)gridDim.x * blockDim.x) {
+        unsigned word = 0;
+        for (int b = 0; b < 32; b++) {
+            const int64_t i = wi * 32 + b;
+            if (i < n && rp[i + 1] - rp[i] > (Off)HUB_DEG) word |= 1u << b;
+        }
+        hubbits[wi] = word;
+        c += __popc(word);
+    }
+    if (c) atomicAdd(count, c);
 }
 
 // ------------------------------------------------------------- host side
@@ -678,38 +707,67 @@ static int push_grid(int device)
     return cached;
 }
 
+// Buffers derived from the graph's degrees: static hub bit mask, hub list
+// and hub-piece queue capacities.  Called at creation and after updates.
+di_status state_prepare_graph(di_graph_s *g, di_state_s *st, cudaStream_t s)
+{
+    const int64_t words = st->ntiles * TILE / 32;
+    Temps t(s);
+    unsigned long long *cnt;
+    DI_TRY(t.get(&cnt, 1));
+    DI_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), s));
+    k_hubbits<<<grid_for(words, 256), 256, 0, s>>>(static_cast<const Off *>(g->rp), g->n, words, st->hubbits,
+                                                   cnt);
+    count_launches(1);
+    DI_CUDA(cudaGetLastError());
+    unsigned long long nh = 0;
+    DI_CUDA(cudaMemcpyAsync(&nh, cnt, sizeof(nh), cudaMemcpyDeviceToHost, s));
+    DI_CUDA(cudaStreamSynchronize(s));
+    if ((int64_t)nh + 1 > st->nhub_cap) {
+        dfree(st->hub_list, s);
+        st->hub_list = nullptr;
+        DI_TRY(dalloc_t(&st->hub_list, nh + 1, s));
+        st->nhub_cap = (int64_t)nh + 1;
+    }
+    const int64_t need = g->nnz / PIECE + (int64_t)nh + 2;
+    if (need > st->max_items) {
+        dfree(st->pc_row, s);
+        dfree(st->pc_len, s);
+        dfree(st->pc_val, s);
+        st->pc_row = st->pc_len = nullptr;
+        st->pc_val = nullptr;
+        DI_TRY(dalloc_t(&st->pc_row, need, s));
+        DI_TRY(dalloc_t(&st->pc_len, need, s));
+        DI_TRY(dalloc_t(&st->pc_val, need, s));
+        st->max_items = need;
+    }
+    return DI_OK;
+}
+
 di_status state_alloc(di_state_s *st, cudaStream_t s)
 {
     di_graph_s *g = st->g;
     const int64_t n = g->n;
     st->ntiles = (n + TILE - 1) / TILE;
-    st->max_items = g->nnz / PIECE + g->nnz / HUB_DEG + 2;
     const int64_t slots = st->ntiles * TILE;
     DI_TRY(dalloc_t(&st->F, slots, s));
     DI_TRY(dalloc_t(&st->H, slots, s));
     DI_TRY(dalloc_t(&st->dscale, n, s));
-    DI_TRY(dalloc_t(&st->ent_row, n, s));
-    DI_TRY(dalloc_t(&st->ent_deg, n, s));
-    DI_TRY(dalloc_t(&st->ent_val, n, s));
-    DI_TRY(dalloc_t(&st->pc_row, st->max_items, s));
-    DI_TRY(dalloc_t(&st->pc_len, st->max_items, s));
-    DI_TRY(dalloc_t(&st->pc_val, st->max_items, s));
+    DI_TRY(dalloc_t(&st->mask, slots / 32, s));
+    DI_TRY(dalloc_t(&st->hubbits, slots / 32, s));
     DI_TRY(dalloc_t(&st->tile_cnt, st->ntiles, s));
-    DI_TRY(dalloc_t(&st->tile_edges, st->ntiles, s));
     DI_TRY(dalloc_t(&st->tile_diff, st->ntiles, s));
     DI_TRY(dalloc_t(&st->tile_fx, 2 * st->ntiles, s));
     DI_TRY(dalloc_t(&st->tile_max, st->ntiles, s));
-    DI_TRY(dalloc_t(&st->lb_status, st->ntiles, s));
-    DI_TRY(dalloc_t(&st->lb_epoch, 1, s));
     DI_TRY(dalloc_t(&st->tile_l1, st->ntiles, s));
     DI_TRY(dalloc_t(&st->tile_l, st->ntiles, s));
     DI_TRY(dalloc_t(&st->ctl, 1, s));
     DI_TRY(dalloc_t(&st->stats, 2 * STAT_CAP, s));
     DI_CUDA(cudaMemsetAsync(st->ctl, 0, sizeof(DevCtl), s));
-    DI_CUDA(cudaMemsetAsync(st->lb_status, 0, sizeof(unsigned long long) * st->ntiles, s));
-    DI_CUDA(cudaMemsetAsync(st->lb_epoch, 0, sizeof(unsigned), s));
+    DI_CUDA(cudaMemsetAsync(st->mask, 0, sizeof(unsigned) * (slots / 32), s));
     DI_CUDA(cudaMemsetAsync(st->F, 0, sizeof(double) * slots, s));
     DI_CUDA(cudaMemsetAsync(st->H, 0, sizeof(double) * slots, s));
+    DI_TRY(state_prepare_graph(g, st, s));
     DI_CUDA(cudaMallocHost(reinterpret_cast<void **>(&st->host_ctl), sizeof(DevCtl)));
     memset(st->host_ctl, 0, sizeof(DevCtl));
     DI_CUDA(cudaEventCreate(&st->ev0));
@@ -723,10 +781,9 @@ di_status state_free(di_state_s *st)
     cudaStream_t s = 0;
     if (st->gexec) cudaGraphExecDestroy(st->gexec);
     if (st->gstream) cudaStreamDestroy(st->gstream);
-    void *bufs[] = {st->F, st->H, st->dscale, st->ent_row, st->ent_deg, st->ent_val, st->pc_row,
-                    st->pc_len, st->pc_val, st->tile_cnt, st->tile_edges, st->tile_diff, st->tile_fx,
-                    st->tile_max, st->lb_status, st->lb_epoch, st->tile_l1, st->tile_l, st->ctl,
-                    st->stats};
+    void *bufs[] = {st->F, st->H, st->dscale, st->mask, st->hubbits, st->hub_list, st->pc_row, st->pc_len,
+                    st->pc_val, st->tile_cnt, st->tile_diff, st->tile_fx, st->tile_max, st->tile_l1,
+                    st->tile_l, st->ctl, st->stats};
     for (void *p : bufs) dfree(p, s);
     if (st->host_ctl) cudaFreeHost(st->host_ctl);
     if (st->ev0) cudaEventDestroy(st->ev0);
@@ -742,24 +799,33 @@ di_status state_free(di_state_s *st)
 static void launch_select(di_graph_s *g, di_state_s *st, cudaStream_t s, int use_cond,
                           cudaGraphConditionalHandle h, int32_t *sel_ids = nullptr)
 {
-    k_select<<<(unsigned)st->ntiles, SEL_THREADS, 0, s>>>(
-        static_cast<const Off *>(g->rp), st->dscale, st->F, st->H, g->n, st->ntiles, st->ent_row,
-        st->ent_deg, st->ent_val, st->pc_row, st->pc_len, st->pc_val, st->tile_cnt, st->tile_edges,
-        st->tile_diff, st->tile_fx, st->tile_max, st->lb_status, st->lb_epoch, st->ctl, use_cond, h,
-        sel_ids, st->stats);
+    k_select<<<(unsigned)st->ntiles, SEL_THREADS, 0, s>>>(st->F, g->n, st->mask, st->hubbits, st->hub_list,
+                                                          st->tile_cnt, st->tile_diff, st->tile_fx,
+                                                          st->tile_max, st->ctl, use_cond, h, sel_ids);
+    count_launches(1);
+}
+
+static void launch_plan(di_graph_s *g, di_state_s *st, cudaStream_t s, int use_cond,
+                        cudaGraphConditionalHandle h)
+{
+    k_plan<<<PLAN_CTAS, SEL_THREADS, 0, s>>>(st->F, st->H, static_cast<const Off *>(g->rp), st->dscale, g->n,
+                                             st->ntiles, st->hub_list, st->pc_row, st->pc_len, st->pc_val,
+                                             st->tile_cnt, st->tile_diff, st->tile_fx, st->tile_max, st->ctl,
+                                             use_cond, h, st->stats);
     count_launches(1);
 }
 
 static void launch_push(di_graph_s *g, di_state_s *st, cudaStream_t s)
 {
     const int grid = push_grid(st->device);
+    const int64_t ngroups = st->ntiles * TILE / 32;
+    const Off *rp = static_cast<const Off *>(g->rp);
     if (g->weighted)
-        k_push<true><<<grid, PUSH_THREADS, 0, s>>>(st->ent_row, st->ent_deg, st->ent_val, st->pc_row,
-                                                  st->pc_len, st->pc_val, g->col, g->w, st->F, st->ctl);
+        k_push<true><<<grid, PUSH_THREADS, 0, s>>>(st->F, st->H, rp, st->dscale, st->mask, st->pc_row,
+                                                  st->pc_len, st->pc_val, ngroups, g->col, g->w, st->ctl);
     else
-        k_push<false><<<grid, PUSH_THREADS, 0, s>>>(st->ent_row, st->ent_deg, st->ent_val, st->pc_row,
-                                                   st->pc_len, st->pc_val, g->col, nullptr, st->F,
-                                                   st->ctl);
+        k_push<false><<<grid, PUSH_THREADS, 0, s>>>(st->F, st->H, rp, st->dscale, st->mask, st->pc_row,
+                                                   st->pc_len, st->pc_val, ngroups, g->col, nullptr, st->ctl);
     count_launches(1);
 }
 
@@ -792,6 +858,7 @@ static di_status build_graph_exec(di_graph_s *g, di_state_s *st)
                                       cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
         launch_select(g, st, st->gstream, 1, h);
+        launch_plan(g, st, st->gstream, 1, h);
         launch_push(g, st, st->gstream);
         cudaGraph_t out = nullptr;
         e = cudaStreamEndCapture(st->gstream, &out);
@@ -868,6 +935,7 @@ di_status solve_loop(di_graph_s *g, di_state_s *st, double tol, const di_opts *o
         for (;;) {
             for (int k = 0; k < o->check_every; k++) {
                 launch_select(g, st, s, 0, cudaGraphConditionalHandle{});
+                launch_plan(g, st, s, 0, cudaGraphConditionalHandle{});
                 if (o->profile && npairs < STAT_CAP) {
                     while (st->npev < 2 * (npairs + 1)) DI_CUDA(cudaEventCreate(&st->pev[st->npev++]));
                     DI_CUDA(cudaEventRecord(st->pev[2 * npairs], s));
@@ -894,7 +962,7 @@ di_status solve_loop(di_graph_s *g, di_state_s *st, double tol, const di_opts *o
     DI_CUDA(cudaStreamSynchronize(s));
     float ms = 0.f;
     DI_CUDA(cudaEventElapsedTime(&ms, st->ev0, st->ev1));
-    if (graph_mode) count_launches(2 * (hc->sweep > 0 ? (int64_t)hc->sweep : 1));
+    if (graph_mode) count_launches(3 * ((int64_t)hc->sweep + 1));
     if (npairs) {
         // push launch i follows selection i; selections past the converged
         // sweep returned at once and their pushes found no work
@@ -925,7 +993,7 @@ di_status solve_loop(di_graph_s *g, di_state_s *st, double tol, const di_opts *o
         info->push_edges = push_edges;
         info->push_entries = push_entries;
     }
-    if (hc->err || hc->done == 3) return DI_ERR_DEVICE_TIMEOUT;
+    if (hc->err) return DI_ERR_DEVICE_TIMEOUT;
     if (hc->done == 2) return DI_ERR_NOT_CONVERGED;
     if (hc->done != 1) return DI_ERR_CUDA;
     return DI_OK;
