@@ -199,6 +199,29 @@ di_status di_frontier_select(di_graph_t g, const double *F, double theta, int32_
  * result does not depend on launch timing). */
 di_status di_residual_l1(di_graph_t g, const double *v, double *out, int mem, void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Allocation-free variant (no counterpart in the paper).
+ *
+ * di_residual_l1_noalloc computes exactly what di_residual_l1 computes (same
+ * kernel, same fixed summation order, same result bit for bit) without
+ * allocating any memory.  It is meant for callers that must not allocate on
+ * the device: a serving loop whose device memory is entirely reserved by its
+ * own pool, or a caller that cannot afford the implicit device-wide
+ * synchronisation that cudaMalloc / cudaFree may cause.
+ *   v       float64[n] in DEVICE memory (host vectors are refused: staging
+ *           them would need an allocation)
+ *   out     host double receiving |v|_1
+ * Scratch: one static device array of about 1 MiB in libdi.so, present on
+ * every device that loads the library until the process exits; it limits the
+ * graph to n <= 2^16 * 2048 = 134,217,728 nodes (larger graphs return
+ * DI_ERR_INVALID_ARG).  The first call made on a device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture on the device.  Every call clears the
+ * part of the array it relies on, but all calls share the one array: calls
+ * whose GPU work overlaps (other streams, other host threads) race and must
+ * be serialised by the caller.  Returns after the result is on the host. */
+di_status di_residual_l1_noalloc(di_graph_t g, const double *v, double *out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

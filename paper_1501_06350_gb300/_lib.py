@@ -85,6 +85,7 @@ SIGNATURES = {
     "di_state_import": (INT, [P, P, P, ctypes.c_double, INT, P]),
     "di_frontier_select": (INT, [P, P, ctypes.c_double, P, ctypes.POINTER(I64), INT, P]),
     "di_residual_l1": (INT, [P, P, P, INT, P]),
+    "di_residual_l1_noalloc": (INT, [P, P, P, P]),
 }
 
 

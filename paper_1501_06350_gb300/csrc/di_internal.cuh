@@ -199,6 +199,8 @@ di_status state_free(di_state_s *st);
 di_status solve_loop(di_graph_s *g, di_state_s *st, double tol, const di_opts *o, di_info *info,
                      cudaStream_t s, bool fresh, const double *Z_dev);
 di_status l1_device(di_graph_s *g, const double *v, double *out_host, cudaStream_t s);
+di_status l1_device_into(di_graph_s *g, const double *v, double *part_l1, double *part_l, DevCtl *ctl,
+                         double *out_host, cudaStream_t s);
 di_status select_only(di_graph_s *g, const double *F, double theta, int32_t *ids, int64_t *count,
                       cudaStream_t s);
 di_status update_edges(di_graph_s *g, di_state_s *st, int64_t m, const int32_t *src,

@@ -891,6 +891,22 @@ di_status l1_device(di_graph_s *g, const double *v, double *out_host, cudaStream
     return DI_OK;
 }
 
+// The same reduction as l1_device, into buffers the caller provides (the
+// allocation-free entry point passes its static scratch here).
+di_status l1_device_into(di_graph_s *g, const double *v, double *part_l1, double *part_l, DevCtl *ctl,
+                         double *out_host, cudaStream_t s)
+{
+    const int64_t ntiles = (g->n + TILE - 1) / TILE;
+    DI_CUDA(cudaMemsetAsync(ctl, 0, sizeof(DevCtl), s));
+    k_reduce<<<(unsigned)ntiles, SEL_THREADS, 0, s>>>(v, nullptr, static_cast<const Off *>(g->rp), g->n,
+                                                      ntiles, part_l1, part_l, ctl, RED_PLAIN);
+    count_launches(1);
+    DI_CUDA(cudaGetLastError());
+    DI_CUDA(cudaMemcpyAsync(out_host, &ctl->final_l1, sizeof(double), cudaMemcpyDeviceToHost, s));
+    DI_CUDA(cudaStreamSynchronize(s));
+    return DI_OK;
+}
+
 di_status solve_loop(di_graph_s *g, di_state_s *st, double tol, const di_opts *o, di_info *info,
                      cudaStream_t s, bool fresh, const double *Z_dev)
 {
