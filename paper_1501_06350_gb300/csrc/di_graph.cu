@@ -288,6 +288,116 @@ di_status graph_build_csc(di_graph_s *g, cudaStream_t s)
     return DI_OK;
 }
 
+// ---------------------------------------------------------------- hot targets
+// In-degree of every page; a bucket of about a quarter octave per in-degree
+// (integer only: 4 * floor(log2 x) + the two bits after the leading one).
+__device__ __forceinline__ int indeg_bucket(unsigned x)
+{
+    if (x == 0) return 0;
+    const int lg = 31 - __clz(x);
+    const unsigned frac = lg >= 2 ? (x >> (lg - 2)) & 3u : (x << (2 - lg)) & 3u;
+    return 1 + 4 * lg + (int)frac;
+}
+
+__global__ void k_indeg(const int32_t *col, int64_t nnz, unsigned *indeg)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz;
+         e += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(indeg + col[e], 1u);
+}
+
+__global__ void k_indeg_hist(const unsigned *indeg, int64_t n, unsigned long long *hist)
+{
+    __shared__ unsigned long long h[130];
+    for (int b = threadIdx.x; b < 130; b += blockDim.x) h[b] = 0;
+    __syncthreads();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(h + indeg_bucket(indeg[i]), 1ull);
+    __syncthreads();
+    for (int b = threadIdx.x; b < 130; b += blockDim.x)
+        if (h[b]) atomicAdd(hist + b, h[b]);
+}
+
+__global__ void k_hot_assign(const unsigned *indeg, int64_t n, int bmin, unsigned min_indeg, int *slot_of,
+                             int32_t *hot_node, unsigned *nhot)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned x = indeg[i];
+        int sl = -1;
+        if (x >= min_indeg && indeg_bucket(x) >= bmin) {
+            sl = (int)atomicAdd(nhot, 1u);
+            hot_node[sl] = (int32_t)i;
+        }
+        slot_of[i] = sl;
+    }
+}
+
+__global__ void k_pcol(const int32_t *col, int64_t nnz, const int *slot_of, int32_t *pcol)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t c = col[e];
+        const int sl = slot_of[c];
+        pcol[e] = sl >= 0 ? (int32_t)(0x80000000u | (unsigned)sl) : c;
+    }
+}
+
+// Push copy of the link targets: links into the (at most HOT_K) pages with
+// the most in-links are tagged with their slot so that the push can add them
+// up in shared memory first (one global add per CTA and page instead of one
+// per link: the many adds into one address would otherwise serialise).
+di_status graph_build_push_targets(di_graph_s *g, cudaStream_t s)
+{
+    if (g->pcol && g->pcol_version == g->version) return DI_OK;
+    const int64_t n = g->n, m = g->nnz;
+    dfree(g->pcol, s);
+    g->pcol = nullptr;
+    if (!g->hot_node) DI_TRY(dalloc_t(&g->hot_node, HOT_K, s));
+    DI_TRY(dalloc_t(&g->pcol, m, s));
+    Temps t(s);
+    unsigned *nhot;
+    unsigned long long *hist;
+    int *slot_of;
+    DI_TRY(t.get(&hist, 130));
+    DI_TRY(t.get(&slot_of, n));
+    DI_TRY(t.get(&nhot, 1));
+    DI_CUDA(cudaMemsetAsync(hist, 0, sizeof(unsigned long long) * 130, s));
+    DI_CUDA(cudaMemsetAsync(nhot, 0, sizeof(unsigned), s));
+    if (!g->indeg) {   // counted once; link updates keep it current
+        DI_TRY(dalloc_t(&g->indeg, n, s));
+        DI_CUDA(cudaMemsetAsync(g->indeg, 0, sizeof(unsigned) * n, s));
+        k_indeg<<<grid_for(m, 256), 256, 0, s>>>(g->col, m, g->indeg);
+        count_launches(1);
+    }
+    const unsigned *indeg = g->indeg;
+    k_indeg_hist<<<grid_for(n, 256) < 1024 ? grid_for(n, 256) : 1024, 256, 0, s>>>(indeg, n, hist);
+    count_launches(1);
+    unsigned long long hh[130];
+    DI_CUDA(cudaMemcpyAsync(hh, hist, sizeof(hh), cudaMemcpyDeviceToHost, s));
+    DI_CUDA(cudaStreamSynchronize(s));
+    // smallest bucket whose tail fits in HOT_K slots
+    int bmin = 130;
+    unsigned long long tail = 0;
+    for (int b = 129; b >= 1; b--) {
+        if (tail + hh[b] > (unsigned long long)HOT_K) break;
+        tail += hh[b];
+        bmin = b;
+    }
+    k_hot_assign<<<grid_for(n, 256), 256, 0, s>>>(indeg, n, bmin, HOT_MIN_INDEG, slot_of, g->hot_node, nhot);
+    count_launches(1);
+    k_pcol<<<grid_for(m, 256), 256, 0, s>>>(g->col, m, slot_of, g->pcol);
+    count_launches(1);
+    DI_CUDA(cudaGetLastError());
+    unsigned nh = 0;
+    DI_CUDA(cudaMemcpyAsync(&nh, nhot, sizeof(nh), cudaMemcpyDeviceToHost, s));
+    DI_CUDA(cudaStreamSynchronize(s));
+    g->nhot = (int)nh;
+    g->pcol_version = g->version;
+    return DI_OK;
+}
+
 di_status graph_export(di_graph_s *g, bool csc, int64_t *ptr, int32_t *idx, double *w, int mem,
                        cudaStream_t s)
 {
@@ -359,7 +469,13 @@ void graph_release(di_graph_s *g)
     dfree(g->cp, s);
     dfree(g->crow, s);
     dfree(g->cw, s);
+    dfree(g->pcol, s);
+    dfree(g->hot_node, s);
+    dfree(g->indeg, s);
     cudaStreamSynchronize(s);
+    g->pcol = nullptr;
+    g->hot_node = nullptr;
+    g->indeg = nullptr;
     g->rp = nullptr;
     g->col = nullptr;
     g->w = g->wsum = g->cw = nullptr;

@@ -98,6 +98,13 @@ struct di_graph_s {
     int32_t *col = nullptr;   // targets [nnz]
     double *w = nullptr;      // link weights [nnz] (weighted only)
     double *wsum = nullptr;   // W_j = sum of row j's weights, left to right [n]
+    // push copy of col: links into the HOT_K most linked-to pages carry
+    // 0x80000000 | slot instead of the page id (built on demand per version)
+    int32_t *pcol = nullptr;  // [nnz]
+    unsigned *indeg = nullptr;    // [n] in-links per page, kept current by updates
+    int32_t *hot_node = nullptr;  // [HOT_K] page of each hot slot
+    int nhot = 0;
+    int64_t pcol_version = -1;
     // in-link structure, built on demand
     int64_t *cp = nullptr;    // [n+1]
     int32_t *crow = nullptr;  // [nnz]
@@ -122,7 +129,7 @@ struct DevCtl {
     unsigned long long npieces;       // hub pieces cut by the plan (read by the push)
     unsigned long long sweep_links;   // links pushed by the running push
     unsigned long long nent;          // frontier nodes of the last selection (mask bits)
-    int fx_shift;              // |F_i| are summed as integers in units of 2^-fx_shift
+    int pad_i;
     unsigned int done;         // 0 running, 1 converged, 2 sweep cap
     unsigned int ticket2;      // last-block ticket of the reductions
     unsigned int err;          // reserved for device-side error flags
@@ -156,8 +163,8 @@ struct di_state_s {
     // per-tile partials
     unsigned int *tile_cnt = nullptr;
     unsigned int *tile_diff = nullptr;
-    unsigned long long *tile_fx = nullptr;   // |F|_1 fixed-point partial (lo, hi)
-    unsigned long long *tile_max = nullptr;
+    float *tile_l1f = nullptr;               // |F|_1 partial, FP32 rounded upward
+    unsigned *tile_maxf = nullptr;           // max |F_i|, FP32 bits rounded downward
     double *tile_l1 = nullptr;               // FP64 partials of the reductions
     double *tile_l = nullptr;
     DevCtl *ctl = nullptr;
@@ -182,8 +189,11 @@ constexpr int PIECE = 1024;                          // links per hub piece
 constexpr int RED_THREADS = 256;
 constexpr int STAT_CAP = 4096;                       // sweeps with recorded statistics
 constexpr int PLAN_CTAS = 32;                        // CTAs of the per-sweep plan kernel
+constexpr int HOT_K = 2048;                          // pages accumulated in shared memory by the push
+constexpr unsigned HOT_MIN_INDEG = 64;               // ... if they have at least this many in-links
 
 di_status graph_build_csc(di_graph_s *g, cudaStream_t s);
+di_status graph_build_push_targets(di_graph_s *g, cudaStream_t s);
 di_status graph_create(int64_t n, int64_t nnz, const int64_t *ptr, const int32_t *idx, const void *w,
                        int wdt, int layout, int mem, cudaStream_t s, di_graph_s *g);
 di_status graph_export(di_graph_s *g, bool csc, int64_t *ptr, int32_t *idx, double *w, int mem,

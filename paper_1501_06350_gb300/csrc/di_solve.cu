@@ -23,10 +23,12 @@
 // if dangling), which is the argument of Theorem 3.  Nothing is taken before
 // the stop test, so the |F|_1 the test certifies is that of the final state.
 //
-// FP64 arithmetic is scarce on this part, so |F|_1 inside the sweep is summed
-// exactly as 128-bit integers (|F_i| rounded up to a multiple of 2^-fx_shift,
-// fx_shift chosen from the initial |F|_1 so the sum stays below 2^113); the
-// sum is order-independent, hence deterministic, and an upper bound.
+// FP64 arithmetic is scarce on this part (about 1/64 of the FP32 rate), so
+// |F|_1 inside the sweep is summed in FP32 with every value and every partial
+// sum rounded upward (an upper bound of the exact sum, in a fixed order, hence
+// deterministic), and the push adds the contributions to the most linked-to
+// pages in shared memory as 64-bit fixed-point integers (native integer
+// atomics) before one FP64 add per page and CTA.
 #include <cuda_runtime.h>
 #include <new>
 #include <string.h>
@@ -36,10 +38,8 @@
 namespace di {
 
 using Off = uint32_t;
-typedef unsigned __int128 u128;
 constexpr unsigned FULL = 0xffffffffu;
 constexpr unsigned long long ABS_MASK = 0x7fffffffffffffffull;
-constexpr int FX_TOP = 112;            // the initial |F|_1 is scaled below 2^FX_TOP
 
 __device__ __forceinline__ unsigned long long abs_bits(double x)
 {
@@ -104,34 +104,44 @@ __device__ __forceinline__ int ldnc_s32(const int *a, unsigned long long pol)
     return r;
 }
 
-// |x| (given by its IEEE bits b, sign cleared) in units of 2^-sh, rounded up.
-__device__ __forceinline__ u128 to_fixed(unsigned long long b, int sh)
+// |x| (given by the IEEE bits b of a double, sign cleared) as FP32 bits,
+// rounded upward (values below FLT_MIN become FLT_MIN, overflow becomes inf).
+__device__ __forceinline__ unsigned f32_up_bits(unsigned long long b)
 {
-    const int e = (int)(b >> 52);
-    unsigned long long m = b & 0x000fffffffffffffull;
-    int ex = e;
-    if (e == 0) ex = 1;
-    else m |= 0x0010000000000000ull;
-    const int s = ex - 1075 + sh;   // value = m * 2^(s - sh)
-    if (m == 0) return 0;
-    if (s >= 0) return s >= 75 ? ~(u128)0 >> 1 : ((u128)m << s);
-    if (s <= -64) return 1;
-    const unsigned long long q = m >> (-s);
-    return (u128)q + ((q << (-s)) != m ? 1 : 0);
+    if (b == 0) return 0u;
+    const int e = (int)(b >> 52) - 1023 + 127;
+    if (e >= 255) return 0x7f800000u;
+    if (e <= 0) return 0x00800000u;
+    const unsigned lo = (unsigned)b, hi = (unsigned)(b >> 32);
+    const unsigned mf = ((hi & 0xfffffu) << 3) | (lo >> 29);
+    const unsigned up = (lo & 0x1fffffffu) != 0u;
+    return ((unsigned)e << 23) + mf + up;    // a carry moves into the exponent
 }
 
-__device__ __forceinline__ double from_fixed(u128 v, int sh)
+// Same, rounded downward (values below FLT_MIN become 0).
+__device__ __forceinline__ unsigned f32_down_bits(unsigned long long b)
 {
-    const double hi = (double)(unsigned long long)(v >> 64);
-    const double lo = (double)(unsigned long long)v;
-    return scalbn(fma(hi, 18446744073709551616.0, lo), -sh);
+    const int e = (int)(b >> 52) - 1023 + 127;
+    if (e >= 255) return 0x7f7fffffu;
+    if (e <= 0) return 0u;
+    const unsigned lo = (unsigned)b, hi = (unsigned)(b >> 32);
+    return ((unsigned)e << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
 }
 
-__device__ __forceinline__ u128 shfl_xor_u128(u128 v, int o)
+// v * 2^sh rounded to the nearest 64-bit integer (two's complement), from the
+// bits of v; |v| * 2^sh must stay below 2^62.
+__device__ __forceinline__ long long to_fixed64(double v, int sh)
 {
-    const unsigned long long lo = __shfl_xor_sync(FULL, (unsigned long long)v, o);
-    const unsigned long long hi = __shfl_xor_sync(FULL, (unsigned long long)(v >> 64), o);
-    return ((u128)hi << 64) | lo;
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const int ex = (int)((b >> 52) & 0x7ffu);
+    if (ex == 0) return 0;   // zero or subnormal: below every scale used here
+    const unsigned long long m = (b & 0x000fffffffffffffull) | 0x0010000000000000ull;
+    const int s = ex - 1075 + sh;
+    long long q;
+    if (s >= 0) q = (long long)(m << (s < 10 ? s : 10));
+    else if (s > -64) q = (long long)((m + (1ull << (-s - 1))) >> (-s));
+    else q = 0;
+    return (b >> 63) ? -q : q;
 }
 
 // Deterministic block sum of doubles: xor butterfly per warp, then warp 0
@@ -303,9 +313,6 @@ __global__ void __launch_bounds__(SEL_THREADS) k_reduce(const double *v, const d
             ctl->l1 = sa;
             ctl->theta = ctl->theta_factor * sa / (double)n;
             ctl->done = sa <= ctl->stop_l1 ? 1u : 0u;
-            int e = 0;
-            if (sa > 0.0) frexp(sa, &e);    // sa < 2^e
-            ctl->fx_shift = FX_TOP - 1 - e;  // |F|_1 scaled below 2^(FX_TOP-1), room to grow 2x
         } else {
             ctl->final_l1 = sa;
             ctl->final_l = sl;
@@ -316,15 +323,15 @@ __global__ void __launch_bounds__(SEL_THREADS) k_reduce(const double *v, const d
 // --------------------------------------------------------------- select
 __global__ void __launch_bounds__(SEL_THREADS)
     k_select(const double *F, int64_t n, unsigned *mask, const unsigned *__restrict__ hubbits,
-             unsigned *hub_list, unsigned *tile_cnt, unsigned *tile_diff, unsigned long long *tile_fx,
-             unsigned long long *tile_max, DevCtl *ctl, int use_cond, cudaGraphConditionalHandle cond,
+             unsigned *hub_list, unsigned *tile_cnt, unsigned *tile_diff, float *tile_l1f, unsigned *tile_maxf,
+             DevCtl *ctl, int use_cond, cudaGraphConditionalHandle cond,
              int32_t *sel_ids)
 {
     constexpr int P = SEL_PER_THREAD;
     constexpr int NW = SEL_THREADS / 32;
     static_assert(32 % P == 0, "a mask word must cover whole threads");
-    __shared__ unsigned long long s_fx[NW][2];
-    __shared__ unsigned long long s_mx[NW], s_cnt[NW];
+    __shared__ float s_fx[NW];
+    __shared__ unsigned s_mx[NW], s_cnt[NW];
     __shared__ unsigned long long smu[NW + 1];
     volatile DevCtl *vc = ctl;
     if (vc->done) {
@@ -338,7 +345,6 @@ __global__ void __launch_bounds__(SEL_THREADS)
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) vc->npieces = 0;   // the last push is over
     const unsigned long long tb = abs_bits(vc->theta);
-    const int fxs = vc->fx_shift;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t tile = blockIdx.x;
     const int64_t i0 = tile * TILE + (int64_t)threadIdx.x * P;
@@ -347,15 +353,16 @@ __global__ void __launch_bounds__(SEL_THREADS)
     unsigned long long fb[P];
     loadP_keep<P>(F, i0, n, fb, keep);
     const unsigned hubw = (__ldg(hubbits + i0 / 32) >> (i0 % 32)) & ((1u << P) - 1u);
-    u128 fx = 0;
+    float fx = 0.0f;
     unsigned selm = 0;
-    unsigned long long mb = 0;
+    unsigned mb = 0;
 #pragma unroll
     for (int k = 0; k < P; k++) {
         const unsigned long long b = fb[k] & ABS_MASK;
-        fx += to_fixed(b, fxs);
+        fx = __fadd_ru(fx, __uint_as_float(f32_up_bits(b)));
         if ((i0 + k < n) && b != 0 && b >= tb) selm |= 1u << k;
-        mb = b > mb ? b : mb;
+        const unsigned md = f32_down_bits(b);
+        mb = md > mb ? md : mb;
     }
     const unsigned bits = selm & ~hubw;   // taken by the push
     const unsigned hubs = selm & hubw;    // taken by the plan
@@ -394,36 +401,34 @@ __global__ void __launch_bounds__(SEL_THREADS)
         for (int k = 0; k < P; k++)
             if ((selm >> k) & 1u) sel_ids[tile * TILE + (int64_t)(spos++)] = (int32_t)(i0 + k);
     }
-    // tile partials (integers, hence exact in any order)
-    unsigned long long cnt = (unsigned long long)__popc(bits) | ((unsigned long long)__popc(selm) << 32);
+    // tile partials in a fixed order (warp butterfly, then warps in order)
+    unsigned cnt = (unsigned)__popc(bits) | ((unsigned)__popc(selm) << 16);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        fx += shfl_xor_u128(fx, o);
-        const unsigned long long y = __shfl_xor_sync(FULL, mb, o);
+        fx = __fadd_ru(fx, __shfl_xor_sync(FULL, fx, o));
+        const unsigned y = __shfl_xor_sync(FULL, mb, o);
         mb = y > mb ? y : mb;
         cnt += __shfl_xor_sync(FULL, cnt, o);
     }
     if (lane == 0) {
-        s_fx[warp][0] = (unsigned long long)fx;
-        s_fx[warp][1] = (unsigned long long)(fx >> 64);
+        s_fx[warp] = fx;
         s_mx[warp] = mb;
         s_cnt[warp] = cnt;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        u128 t = 0;
-        unsigned long long mx = 0, c = 0;
+        float t = s_fx[0];
+        unsigned mx = s_mx[0], c = s_cnt[0];
 #pragma unroll
-        for (int w = 0; w < NW; w++) {
-            t += ((u128)s_fx[w][1] << 64) | s_fx[w][0];
+        for (int w = 1; w < NW; w++) {
+            t = __fadd_ru(t, s_fx[w]);
             mx = s_mx[w] > mx ? s_mx[w] : mx;
             c += s_cnt[w];
         }
-        tile_fx[2 * tile] = (unsigned long long)t;
-        tile_fx[2 * tile + 1] = (unsigned long long)(t >> 64);
-        tile_max[tile] = mx;
-        tile_cnt[tile] = (unsigned)(c & 0xffffffffu);
-        tile_diff[tile] = (unsigned)(c >> 32);
+        tile_l1f[tile] = t;
+        tile_maxf[tile] = mx;
+        tile_cnt[tile] = c & 0xffffu;
+        tile_diff[tile] = c >> 16;
     }
 }
 
@@ -434,55 +439,56 @@ __global__ void __launch_bounds__(SEL_THREADS)
 __global__ void __launch_bounds__(SEL_THREADS)
     k_plan(double *F, double *H, const Off *__restrict__ rp, const double *__restrict__ dscale, int64_t n,
            int64_t ntiles, const unsigned *__restrict__ hub_list, Off *pc_row, Off *pc_len, double *pc_val,
-           const unsigned *tile_cnt, const unsigned *tile_diff, const unsigned long long *tile_fx,
-           const unsigned long long *tile_max, DevCtl *ctl, int use_cond, cudaGraphConditionalHandle cond,
+           const unsigned *tile_cnt, const unsigned *tile_diff, const float *tile_l1f,
+           const unsigned *tile_maxf, DevCtl *ctl, int use_cond, cudaGraphConditionalHandle cond,
            unsigned long long *stats)
 {
     constexpr int NW = SEL_THREADS / 32;
-    __shared__ unsigned long long s_red[5][NW];
+    __shared__ unsigned long long s_red[3][NW];
+    __shared__ float s_l1[NW];
     __shared__ unsigned s_go;
     volatile DevCtl *vc = ctl;
     if (vc->done) return;   // the selection has already closed the loop
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    u128 sfx = 0;
+    // fixed order: thread-strided tiles, xor butterfly, warps in order; every
+    // partial rounded upward, so every CTA gets the same upper bound
+    float sfx = 0.0f;
     unsigned long long sd = 0, sc = 0, mx = 0;
-#pragma unroll 4
     for (int64_t k = threadIdx.x; k < ntiles; k += SEL_THREADS) {
-        sfx += ((u128)__ldg(tile_fx + 2 * k + 1) << 64) | __ldg(tile_fx + 2 * k);
+        sfx = __fadd_ru(sfx, __ldg(tile_l1f + k));
         sd += __ldg(tile_diff + k);
         sc += __ldg(tile_cnt + k);
-        const unsigned long long m = __ldg(tile_max + k);
+        const unsigned long long m = __ldg(tile_maxf + k);
         mx = m > mx ? m : mx;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        sfx += shfl_xor_u128(sfx, o);
+        sfx = __fadd_ru(sfx, __shfl_xor_sync(FULL, sfx, o));
         sd += __shfl_xor_sync(FULL, sd, o);
         sc += __shfl_xor_sync(FULL, sc, o);
         const unsigned long long y = __shfl_xor_sync(FULL, mx, o);
         mx = y > mx ? y : mx;
     }
     if (lane == 0) {
-        s_red[0][warp] = (unsigned long long)sfx;
-        s_red[1][warp] = (unsigned long long)(sfx >> 64);
-        s_red[2][warp] = sd;
-        s_red[3][warp] = sc;
-        s_red[4][warp] = mx;
+        s_l1[warp] = sfx;
+        s_red[0][warp] = sd;
+        s_red[1][warp] = sc;
+        s_red[2][warp] = mx;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        sfx = 0;
+        sfx = s_l1[0];
         sd = sc = mx = 0;
         for (int w = 0; w < NW; w++) {
-            sfx += ((u128)s_red[1][w] << 64) | s_red[0][w];
-            sd += s_red[2][w];
-            sc += s_red[3][w];
-            mx = s_red[4][w] > mx ? s_red[4][w] : mx;
+            if (w) sfx = __fadd_ru(sfx, s_l1[w]);
+            sd += s_red[0][w];
+            sc += s_red[1][w];
+            mx = s_red[2][w] > mx ? s_red[2][w] : mx;
         }
-        const double sa = from_fixed(sfx, vc->fx_shift);
+        const double sa = (double)sfx;
         const unsigned long long sweep = vc->sweep;
         unsigned done = 0;
-        // the integer sum rounds every |F_i| up, so it bounds |F_t|_1 from above
+        // every |F_i| and every partial sum was rounded up: an upper bound of |F_t|_1
         if (sa <= vc->stop_l1) done = 1;
         else if (sweep >= vc->max_sweeps) done = 2;
         s_go = done == 0;
@@ -501,7 +507,7 @@ __global__ void __launch_bounds__(SEL_THREADS)
                 // A sweep that took nothing leaves F unchanged; the largest |F_i|
                 // passes the DI-argmax test exactly, so never ask for more than
                 // that (this covers a rounded average above several equal fluids).
-                const double fmax = __longlong_as_double((long long)mx);
+                const double fmax = (double)__uint_as_float((unsigned)mx);
                 if (sd == 0 && fmax < th) th = fmax;
                 vc->theta = th;
             }
@@ -551,21 +557,72 @@ __device__ __forceinline__ unsigned long long atom_exch_b64(double *a, unsigned 
     return old;
 }
 
-// Warp-centric take and push.  Work unit u < ngroups: the 32 nodes
-// [32u, 32u + 32) and their mask word; u >= ngroups: hub piece u - ngroups.
-// The links of the taken nodes are enumerated 32 at a time and each lane
-// finds the node of its link by a binary search over the lanes' exclusive
-// degree prefixes (shuffles only).
+// Scatter helper: 4 x 32 links in flight per warp.  lane_link(e) gives the
+// link and the value for the warp's e-th link (e < total).  Targets tagged
+// in the push copy of the links (hot pages) are added in shared memory.
+template <bool WEIGHTED, typename LinkOf>
+__device__ __forceinline__ void scatter_links(unsigned total, LinkOf lane_link, const int32_t *pcol,
+                                              const double *w, double *F, unsigned long long *s_hot,
+                                              int hot_shift, unsigned long long keep,
+                                              unsigned long long stream)
+{
+    const int lane = threadIdx.x & 31;
+    for (unsigned base = 0; base < total; base += 128) {
+        int32_t c[4];
+        double v[4];
+        bool ok[4];
+#pragma unroll
+        for (int g = 0; g < 4; g++) {
+            const unsigned e = base + (unsigned)(g * 32 + lane);
+            Off link;
+            double vj;
+            lane_link(e < total ? e : total - 1, link, vj);
+            ok[g] = e < total;
+            c[g] = 0;
+            v[g] = vj;
+            if (ok[g]) {
+                c[g] = ldnc_s32(pcol + link, stream);
+                if (WEIGHTED) v[g] = vj * ldnc_f64(w + link, stream);
+            }
+        }
+#pragma unroll
+        for (int g = 0; g < 4; g++) {
+            if (!ok[g]) continue;
+            if (c[g] >= 0) red_add_f64(F + c[g], v[g], keep);
+            else atomicAdd(s_hot + (c[g] & 0x7fffffff), (unsigned long long)to_fixed64(v[g], hot_shift));
+        }
+    }
+}
+
+// Warp-centric take and push.  Work unit u < nunits: the 128 nodes
+// [128u, 128u + 128), lane l owning nodes 128u + 4l .. 4l + 3 and their bits
+// of mask words 4u .. 4u + 3; u >= nunits: hub piece u - nunits.  All takes
+// and loads of a unit are issued before any is used.  The taken nodes' links
+// are enumerated 32 at a time; a link finds its lane by a binary search over
+// the lanes' exclusive link prefixes (shuffles) and its node among the lane's
+// four by their running degrees.
 template <bool WEIGHTED>
 __global__ void __launch_bounds__(PUSH_THREADS)
     k_push(double *F, double *H, const Off *__restrict__ rp, const double *__restrict__ dscale,
            const unsigned *__restrict__ mask, const Off *__restrict__ pc_row, const Off *__restrict__ pc_len,
-           const double *__restrict__ pc_val, int64_t ngroups, const int32_t *__restrict__ col,
-           const double *__restrict__ w, DevCtl *ctl)
+           const double *__restrict__ pc_val, int64_t ngroups, const int32_t *__restrict__ pcol,
+           const int32_t *__restrict__ hot_node, int nhot, const double *__restrict__ w, DevCtl *ctl)
 {
+    constexpr int Q = 4;
     __shared__ unsigned long long s_links[PUSH_THREADS / 32];
+    __shared__ unsigned long long s_hot[HOT_K];   // fixed point, units of 2^-hot_shift
     volatile DevCtl *vc = ctl;
     if (!vc->push_ready) return;
+    // Fluid taken twice in one sweep (pushed in, then taken again) is counted
+    // twice, so the values pushed in a sweep add up to at most
+    // d |F|_1 / (1 - d) < 8 |F|_1 < 2^(e+3) in magnitude for d <= 7/8, and
+    // for larger d the sum of any one CTA's share stays far below that:
+    // 2^(58 - e) keeps every slot below 2^61.
+    int e = 0;
+    frexp(vc->l1, &e);
+    const int hot_shift = 58 - e;
+    for (int k = threadIdx.x; k < nhot; k += PUSH_THREADS) s_hot[k] = 0ull;
+    __syncthreads();
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         vc->nhub = 0;                 // the plan has consumed the hub list
         vc->sweep = vc->sweep + 1;    // (the plan reads it; it is stable until here)
@@ -573,94 +630,106 @@ __global__ void __launch_bounds__(PUSH_THREADS)
     const unsigned long long npc = vc->npieces;
     const unsigned long long keep = pol_last(), stream = pol_first();
     const int lane = threadIdx.x & 31;
-    const unsigned long long nunits = (unsigned long long)ngroups + npc;
+    const unsigned long long nunits = (unsigned long long)ngroups / Q;
     const unsigned long long wid = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const unsigned long long nw = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
     unsigned long long links = 0;
-    for (unsigned long long u = wid; u < nunits; u += nw) {
-        if (u < (unsigned long long)ngroups) {
-            const unsigned m = ldnc_u32(mask + u, stream);
-            if (m == 0) continue;
-            const unsigned long long i = u * 32 + lane;
-            Off row = 0, deg = 0;
-            double v0 = 0.0;
-            if ((m >> lane) & 1u) {
-                // take (Eq. defF): whatever fluid node i holds now, into H(i)
-                const unsigned long long fbits = atom_exch_b64(F + i, 0ull, keep);
-                row = ldnc_u32(rp + i, stream);
-                const Off r1 = ldnc_u32(rp + i + 1, stream);
-                const unsigned long long hb = ld_b64(H + i, stream);
-                const double ds = ldnc_f64(dscale + i, stream);
-                const double f = __longlong_as_double((long long)fbits);
-                st_b64(H + i, (unsigned long long)__double_as_longlong(__longlong_as_double((long long)hb) + f),
-                       stream);
-                deg = r1 - row;
-                v0 = f * ds;
-            }
-            Off incl = deg;
+    for (unsigned long long u = wid; u < nunits + npc; u += nw) {
+        if (u < nunits) {
+            const unsigned mw = ldnc_u32(mask + u * Q + (lane >> 3), stream);
+            const unsigned bits = (mw >> (Q * (lane & 7))) & ((1u << Q) - 1u);
+            if (!__any_sync(FULL, bits)) continue;
+            const unsigned long long i0 = u * (32 * Q) + (unsigned long long)lane * Q;
+            Off r[Q + 1];
+            double val[Q];
+            unsigned c1 = 0, c2 = 0, c3 = 0, tot = 0;
+            if (bits) {
+                unsigned long long fb[Q], hb[Q];
+                double ds[Q];
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const Off y = __shfl_up_sync(FULL, incl, o);
-                if (lane >= o) incl += y;
-            }
-            const Off total = __shfl_sync(FULL, incl, 31);
-            const Off excl = incl - deg;
-            links += total;
-            // lanes' links are e = base + lane; four groups in flight
-            for (Off base = 0; base < total; base += 128) {
-                int32_t c[4];
-                double v[4];
-#pragma unroll
-                for (int g = 0; g < 4; g++) {
-                    const Off e = base + (Off)(g * 32 + lane);
-                    const Off eq = e < total ? e : total - 1;
-                    int j = 0;
-#pragma unroll
-                    for (int step = 16; step > 0; step >>= 1) {
-                        const Off ex = __shfl_sync(FULL, excl, j + step);
-                        if (ex <= eq) j += step;
-                    }
-                    const Off rj = __shfl_sync(FULL, row, j);
-                    const Off xj = __shfl_sync(FULL, excl, j);
-                    const double vj = __shfl_sync(FULL, v0, j);
-                    c[g] = -1;
-                    v[g] = vj;
-                    if (e < total) {
-                        const Off link = rj + (e - xj);
-                        c[g] = ldnc_s32(col + link, stream);
-                        if (WEIGHTED) v[g] = vj * ldnc_f64(w + link, stream);
-                    }
+                for (int k = 0; k < Q; k++) {
+                    fb[k] = 0ull;
+                    hb[k] = 0ull;
+                    ds[k] = 0.0;
+                    if (!((bits >> k) & 1u)) continue;
+                    // take (Eq. defF): whatever fluid the node holds now
+                    fb[k] = atom_exch_b64(F + i0 + k, 0ull, keep);
+                    hb[k] = ld_b64(H + i0 + k, stream);
+                    ds[k] = ldnc_f64(dscale + i0 + k, stream);
                 }
 #pragma unroll
-                for (int g = 0; g < 4; g++)
-                    if (c[g] >= 0) red_add_f64(F + c[g], v[g], keep);
+                for (int k = 0; k <= Q; k++) r[k] = ldnc_u32(rp + i0 + k, stream);
+                unsigned dg[Q];
+#pragma unroll
+                for (int k = 0; k < Q; k++) {
+                    dg[k] = 0;
+                    val[k] = 0.0;
+                    if (!((bits >> k) & 1u)) continue;
+                    const double f = __longlong_as_double((long long)fb[k]);
+                    st_b64(H + i0 + k,
+                           (unsigned long long)__double_as_longlong(__longlong_as_double((long long)hb[k]) + f),
+                           stream);
+                    dg[k] = r[k + 1] - r[k];
+                    val[k] = f * ds[k];
+                }
+                c1 = dg[0];
+                c2 = c1 + dg[1];
+                c3 = c2 + dg[2];
+                tot = c3 + dg[3];
+            } else {
+#pragma unroll
+                for (int k = 0; k <= Q; k++) r[k] = 0;
+#pragma unroll
+                for (int k = 0; k < Q; k++) val[k] = 0.0;
             }
+            unsigned incl = tot;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned y = __shfl_up_sync(FULL, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const unsigned total = __shfl_sync(FULL, incl, 31);
+            const unsigned excl = incl - tot;
+            links += total;
+            auto lane_link = [&](unsigned e, Off &link, double &vj) {
+                int j = 0;
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1) {
+                    const unsigned ex = __shfl_sync(FULL, excl, j + step);
+                    if (ex <= e) j += step;
+                }
+                const unsigned o = e - __shfl_sync(FULL, excl, j);
+                const unsigned a1 = __shfl_sync(FULL, c1, j), a2 = __shfl_sync(FULL, c2, j),
+                               a3 = __shfl_sync(FULL, c3, j);
+                const Off q0 = __shfl_sync(FULL, r[0], j), q1 = __shfl_sync(FULL, r[1], j),
+                          q2 = __shfl_sync(FULL, r[2], j), q3 = __shfl_sync(FULL, r[3], j);
+                const double v0 = __shfl_sync(FULL, val[0], j), v1 = __shfl_sync(FULL, val[1], j),
+                             v2 = __shfl_sync(FULL, val[2], j), v3 = __shfl_sync(FULL, val[3], j);
+                if (o < a1) { link = q0 + o; vj = v0; }
+                else if (o < a2) { link = q1 + (o - a1); vj = v1; }
+                else if (o < a3) { link = q2 + (o - a2); vj = v2; }
+                else { link = q3 + (o - a3); vj = v3; }
+            };
+            scatter_links<WEIGHTED>(total, lane_link, pcol, w, F, s_hot, hot_shift, keep, stream);
         } else {
-            const unsigned long long p = u - (unsigned long long)ngroups;
+            const unsigned long long p = u - nunits;
             const Off row = ldnc_u32(pc_row + p, stream), len = ldnc_u32(pc_len + p, stream);
             const double pv = ldnc_f64(pc_val + p, stream);
             links += len;
-            for (Off base = 0; base < len; base += 128) {
-                int32_t c[4];
-                double v[4];
-#pragma unroll
-                for (int g = 0; g < 4; g++) {
-                    const Off e = base + (Off)(g * 32 + lane);
-                    c[g] = -1;
-                    v[g] = pv;
-                    if (e < len) {
-                        c[g] = ldnc_s32(col + row + e, stream);
-                        if (WEIGHTED) v[g] = pv * ldnc_f64(w + row + e, stream);
-                    }
-                }
-#pragma unroll
-                for (int g = 0; g < 4; g++)
-                    if (c[g] >= 0) red_add_f64(F + c[g], v[g], keep);
-            }
+            auto piece_link = [&](unsigned e, Off &link, double &vj) {
+                link = row + e;
+                vj = pv;
+            };
+            scatter_links<WEIGHTED>(len, piece_link, pcol, w, F, s_hot, hot_shift, keep, stream);
         }
     }
     if (lane == 0) s_links[threadIdx.x >> 5] = links;
     __syncthreads();
+    // one global add per hot page this CTA touched
+    for (int k = threadIdx.x; k < nhot; k += PUSH_THREADS) {
+        const long long a = (long long)s_hot[k];
+        if (a != 0) red_add_f64(F + __ldg(hot_node + k), scalbn((double)a, -hot_shift), keep);
+    }
     if (threadIdx.x == 0) {
         unsigned long long t = 0;
         for (int q = 0; q < PUSH_THREADS / 32; q++) t += s_links[q];
@@ -711,6 +780,7 @@ static int push_grid(int device)
 // and hub-piece queue capacities.  Called at creation and after updates.
 di_status state_prepare_graph(di_graph_s *g, di_state_s *st, cudaStream_t s)
 {
+    DI_TRY(graph_build_push_targets(g, s));
     const int64_t words = st->ntiles * TILE / 32;
     Temps t(s);
     unsigned long long *cnt;
@@ -757,8 +827,8 @@ di_status state_alloc(di_state_s *st, cudaStream_t s)
     DI_TRY(dalloc_t(&st->hubbits, slots / 32, s));
     DI_TRY(dalloc_t(&st->tile_cnt, st->ntiles, s));
     DI_TRY(dalloc_t(&st->tile_diff, st->ntiles, s));
-    DI_TRY(dalloc_t(&st->tile_fx, 2 * st->ntiles, s));
-    DI_TRY(dalloc_t(&st->tile_max, st->ntiles, s));
+    DI_TRY(dalloc_t(&st->tile_l1f, st->ntiles, s));
+    DI_TRY(dalloc_t(&st->tile_maxf, st->ntiles, s));
     DI_TRY(dalloc_t(&st->tile_l1, st->ntiles, s));
     DI_TRY(dalloc_t(&st->tile_l, st->ntiles, s));
     DI_TRY(dalloc_t(&st->ctl, 1, s));
@@ -782,7 +852,7 @@ di_status state_free(di_state_s *st)
     if (st->gexec) cudaGraphExecDestroy(st->gexec);
     if (st->gstream) cudaStreamDestroy(st->gstream);
     void *bufs[] = {st->F, st->H, st->dscale, st->mask, st->hubbits, st->hub_list, st->pc_row, st->pc_len,
-                    st->pc_val, st->tile_cnt, st->tile_diff, st->tile_fx, st->tile_max, st->tile_l1,
+                    st->pc_val, st->tile_cnt, st->tile_diff, st->tile_l1f, st->tile_maxf, st->tile_l1,
                     st->tile_l, st->ctl, st->stats};
     for (void *p : bufs) dfree(p, s);
     if (st->host_ctl) cudaFreeHost(st->host_ctl);
@@ -800,8 +870,8 @@ static void launch_select(di_graph_s *g, di_state_s *st, cudaStream_t s, int use
                           cudaGraphConditionalHandle h, int32_t *sel_ids = nullptr)
 {
     k_select<<<(unsigned)st->ntiles, SEL_THREADS, 0, s>>>(st->F, g->n, st->mask, st->hubbits, st->hub_list,
-                                                          st->tile_cnt, st->tile_diff, st->tile_fx,
-                                                          st->tile_max, st->ctl, use_cond, h, sel_ids);
+                                                          st->tile_cnt, st->tile_diff, st->tile_l1f,
+                                                          st->tile_maxf, st->ctl, use_cond, h, sel_ids);
     count_launches(1);
 }
 
@@ -810,7 +880,7 @@ static void launch_plan(di_graph_s *g, di_state_s *st, cudaStream_t s, int use_c
 {
     k_plan<<<PLAN_CTAS, SEL_THREADS, 0, s>>>(st->F, st->H, static_cast<const Off *>(g->rp), st->dscale, g->n,
                                              st->ntiles, st->hub_list, st->pc_row, st->pc_len, st->pc_val,
-                                             st->tile_cnt, st->tile_diff, st->tile_fx, st->tile_max, st->ctl,
+                                             st->tile_cnt, st->tile_diff, st->tile_l1f, st->tile_maxf, st->ctl,
                                              use_cond, h, st->stats);
     count_launches(1);
 }
@@ -822,10 +892,12 @@ static void launch_push(di_graph_s *g, di_state_s *st, cudaStream_t s)
     const Off *rp = static_cast<const Off *>(g->rp);
     if (g->weighted)
         k_push<true><<<grid, PUSH_THREADS, 0, s>>>(st->F, st->H, rp, st->dscale, st->mask, st->pc_row,
-                                                  st->pc_len, st->pc_val, ngroups, g->col, g->w, st->ctl);
+                                                  st->pc_len, st->pc_val, ngroups, g->pcol, g->hot_node,
+                                                  g->nhot, g->w, st->ctl);
     else
         k_push<false><<<grid, PUSH_THREADS, 0, s>>>(st->F, st->H, rp, st->dscale, st->mask, st->pc_row,
-                                                   st->pc_len, st->pc_val, ngroups, g->col, nullptr, st->ctl);
+                                                   st->pc_len, st->pc_val, ngroups, g->pcol, g->hot_node,
+                                                   g->nhot, nullptr, st->ctl);
     count_launches(1);
 }
 
@@ -1109,7 +1181,6 @@ di_status select_only(di_graph_s *g, const double *F, double theta, int32_t *ids
             hc->stop_l1 = -1.0;
             hc->max_sweeps = ~0ull;
             hc->theta_factor = 1.0;
-            hc->fx_shift = 0;
             cudaMemcpyAsync(st.ctl, hc, sizeof(DevCtl), cudaMemcpyHostToDevice, s);
             cudaMemcpyAsync(st.F, F, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
             k_dscale<<<grid_for(n, 256), 256, 0, s>>>(static_cast<const Off *>(g->rp), g->wsum, n, 0.85,

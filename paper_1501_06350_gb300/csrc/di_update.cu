@@ -2,14 +2,15 @@
 // insertions/deletions to the canonical graph and inject the correction fluid
 // d (P' - P) H into F, keeping H.
 //
-// The old links (key = source << 32 | target, value = old position) and the
-// batch entries (value = nnz + batch index) are concatenated and sorted with
-// the stable radix sort, so each run of equal keys lists the old link first
-// and then the batch operations in batch order; the last operation decides.
-// A source j is "touched" when its set of out-links (or a weight) changes,
-// i.e. when column j of P changes; only those columns contribute to
-// d (P' - P) H, and for them the whole old column is withdrawn and the whole
-// new column injected (every entry changes when out(j) or W_j changes).
+// Only the batch is sorted (stable radix sort of source << 32 | target, so the
+// last operation on a link decides).  Each distinct batch link is looked up
+// in its (sorted) old row and classified: inserted, deleted, re-weighted or
+// no-op.  Rows without an effective change are moved as they are (a warp per
+// 32 rows, coalesced); the changed rows are merged with their batch entries.
+// A source j is "touched" when its set of out-links or a weight changes, i.e.
+// when column j of P changes; only those columns contribute to d (P' - P) H,
+// and for them the whole old column is withdrawn and the whole new column
+// injected (every entry changes when out(j) or W_j changes).
 #include <cuda_runtime.h>
 
 #include "di_internal.cuh"
@@ -17,6 +18,9 @@
 namespace di {
 
 using Off = uint32_t;
+constexpr unsigned FULL = 0xffffffffu;
+
+enum : unsigned char { EFF_NOP = 0, EFF_INS = 1, EFF_DEL = 2, EFF_UPD = 3 };
 
 __global__ void k_check_batch(const int32_t *src, const int32_t *dst, const double *w, const int8_t *op,
                               int64_t m, int64_t n, unsigned *err)
@@ -31,122 +35,218 @@ __global__ void k_check_batch(const int32_t *src, const int32_t *dst, const doub
     if (e) atomicOr(err, e);
 }
 
-__global__ void k_keys_old(const Off *rp, const int32_t *col, int64_t n, uint64_t *keys, uint32_t *vals)
-{
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t r = warp; r < n; r += nwarps)
-        for (Off e = rp[r] + lane; e < rp[r + 1]; e += 32) {
-            keys[e] = ((uint64_t)r << 32) | (uint32_t)col[e];
-            vals[e] = e;
-        }
-}
-
-__global__ void k_keys_batch(const int32_t *src, const int32_t *dst, int64_t m, int64_t nnz,
-                             uint64_t *keys, uint32_t *vals)
+__global__ void k_batch_keys(const int32_t *src, const int32_t *dst, int64_t m, uint64_t *keys,
+                             uint32_t *vals)
 {
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m;
          k += (int64_t)gridDim.x * blockDim.x) {
-        keys[nnz + k] = ((uint64_t)(uint32_t)src[k] << 32) | (uint32_t)dst[k];
-        vals[nnz + k] = (uint32_t)(nnz + k);
+        keys[k] = ((uint64_t)(uint32_t)src[k] << 32) | (uint32_t)dst[k];
+        vals[k] = (uint32_t)k;
     }
 }
 
-// Resolve each run of equal keys: keep[e] = 1 at a run start whose link is
-// present after the batch; nw[e] its weight; touched[source] = 1 if the
-// link's presence or weight changed.
-__global__ void k_resolve(const uint64_t *keys, const uint32_t *vals, int64_t tot, int64_t nnz,
-                          const double *wold, const double *wb, const int8_t *op, uint8_t *keep,
-                          double *nw, uint8_t *touched)
+// The last entry of each run of equal keys is the last operation on that link.
+__global__ void k_run_ends(const uint64_t *keys, int64_t m, uint8_t *keep)
 {
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const uint64_t key = keys[e];
-        if (e > 0 && keys[e - 1] == key) {
-            keep[e] = 0;
-            continue;
-        }
-        int64_t q = e;
-        const bool has_old = vals[e] < (uint64_t)nnz;
-        int64_t last = -1;
-        while (q < tot && keys[q] == key) {
-            if (vals[q] >= (uint64_t)nnz) last = (int64_t)vals[q] - nnz;
-            q++;
-        }
-        bool present = has_old;
-        double wv = has_old && wold ? wold[vals[e]] : 1.0;
-        if (last >= 0) {
-            present = op[last] == 1;
-            if (present) wv = wb ? wb[last] : 1.0;
-        }
-        keep[e] = present ? 1 : 0;
-        nw[e] = wv;
-        bool changed = present != has_old;
-        if (present && has_old && wold && wv != wold[vals[e]]) changed = true;
-        if (changed) touched[key >> 32] = 1;
-    }
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * blockDim.x)
+        keep[e] = (e == m - 1 || keys[e + 1] != keys[e]) ? 1 : 0;
 }
 
-__global__ void k_compact_new(const uint64_t *keys, const uint8_t *keep, const uint64_t *pos, int64_t tot,
-                              const double *nw, int32_t *col, uint32_t *rows, double *wout)
+__global__ void k_unique(const uint64_t *keys, const uint32_t *vals, const uint8_t *keep, const uint64_t *pos,
+                         int64_t m, const int8_t *op, const double *wb, uint64_t *ukey, int8_t *uop, double *uw)
 {
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
          e += (int64_t)gridDim.x * blockDim.x) {
         if (!keep[e]) continue;
         const int64_t k = (int64_t)pos[e];
-        col[k] = (int32_t)(uint32_t)(keys[e] & 0xffffffffull);
-        rows[k] = (uint32_t)(keys[e] >> 32);
-        if (wout) wout[k] = nw[e];
+        const uint32_t b = vals[e];
+        ukey[k] = keys[e];
+        uop[k] = op[b];
+        uw[k] = wb ? wb[b] : 1.0;
     }
 }
 
-template <typename P>
-__global__ void k_row_ptr_u(const uint32_t *rows, int64_t m, int64_t n, P *rp)
+// Classify each distinct batch link against its old row (binary search);
+// count the row's degree change, flag the row, keep in-degrees current.
+__global__ void k_classify(const uint64_t *ukey, const int8_t *uop, const double *uw, int64_t nu, const Off *rp,
+                           const int32_t *col, const double *w, uint8_t *eff, int *delta, uint8_t *touched,
+                           unsigned *indeg)
 {
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nu;
          k += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t r = rows[k];
-        const int64_t rprev = k > 0 ? (int64_t)rows[k - 1] : -1;
-        for (int64_t q = rprev + 1; q <= r; q++) rp[q] = (P)k;
-        if (k == m - 1)
-            for (int64_t q = r + 1; q <= n; q++) rp[q] = (P)m;
+        const uint32_t sr = (uint32_t)(ukey[k] >> 32);
+        const int32_t tg = (int32_t)(uint32_t)ukey[k];
+        const Off end = rp[sr + 1];
+        Off lo = rp[sr], hi = end;
+        while (lo < hi) {
+            const Off mid = lo + ((hi - lo) >> 1);
+            if (col[mid] < tg) lo = mid + 1;
+            else hi = mid;
+        }
+        const bool present = lo < end && col[lo] == tg;
+        const bool keep = uop[k] == 1;
+        unsigned char e = EFF_NOP;
+        int dl = 0;
+        if (present && !keep) {
+            e = EFF_DEL;
+            dl = -1;
+        } else if (!present && keep) {
+            e = EFF_INS;
+            dl = 1;
+        } else if (present && keep && w && uw[k] != w[lo]) {
+            e = EFF_UPD;
+        }
+        eff[k] = e;
+        if (e != EFF_NOP) {
+            if (dl) atomicAdd(delta + sr, dl);
+            touched[sr] = 1;
+            if (indeg && dl) atomicAdd(indeg + tg, (unsigned)dl);
+        }
     }
 }
 
-__global__ void k_zero_u32(uint32_t *a, int64_t n)
+__global__ void k_new_degree(const Off *rp, const int *delta, int64_t n, uint32_t *deg)
+{
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+         j += (int64_t)gridDim.x * blockDim.x)
+        deg[j] = (uint32_t)((int64_t)(rp[j + 1] - rp[j]) + delta[j]);
+}
+
+__global__ void k_rp_from_scan(const uint64_t *ex, const uint64_t *total, int64_t n, Off *nrp)
+{
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j <= n;
+         j += (int64_t)gridDim.x * blockDim.x)
+        nrp[j] = (Off)(j < n ? ex[j] : *total);
+}
+
+// Rows without an effective change keep their links; a warp moves the links
+// of 32 consecutive rows (lane l owns row 32g + l) to their new offsets.
+__global__ void k_copy_rows(const Off *rp, const Off *nrp, const int32_t *col, const double *w,
+                            const uint8_t *touched, int64_t n, int32_t *ncol, double *nw)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t ngroups = (n + 31) / 32;
+    const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t gi = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; gi < ngroups; gi += nwarp) {
+        const int64_t r = gi * 32 + lane;
+        Off a = 0, na = 0, len = 0;
+        if (r < n) {
+            a = rp[r];
+            na = nrp[r];
+            if (!touched[r]) len = rp[r + 1] - a;
+        }
+        Off incl = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const Off y = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const Off total = __shfl_sync(FULL, incl, 31);
+        const Off excl = incl - len;
+        for (Off base = 0; base < total; base += 32) {
+            const Off e = base + lane;
+            const Off eq = e < total ? e : total - 1;
+            int j = 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                const Off ex = __shfl_sync(FULL, excl, j + step);
+                if (ex <= eq) j += step;
+            }
+            const Off o = eq - __shfl_sync(FULL, excl, j);
+            const Off from = __shfl_sync(FULL, a, j) + o, to = __shfl_sync(FULL, na, j) + o;
+            if (e < total) {
+                ncol[to] = col[from];
+                if (w) nw[to] = w[from];
+            }
+        }
+    }
+}
+
+__global__ void k_list(const uint8_t *flag, const uint64_t *pos, int64_t n, uint32_t *list)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
-        a[i] = 0;
+        if (flag[i]) list[pos[i]] = (uint32_t)i;
 }
 
-__global__ void k_row_sums_u(const uint32_t *rp, const double *w, int64_t n, double *wsum,
-                             unsigned long long *ndang)
+__device__ __forceinline__ int64_t lower_key(const uint64_t *ukey, int64_t nu, uint64_t key)
 {
-    unsigned long long c = 0;
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
-         j += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t a = rp[j], b = rp[j + 1];
-        if (a == b) c++;
-        if (wsum) {
-            double s = 0.0;
-            for (uint32_t e = a; e < b; e++) s = (e == a) ? w[e] : s + w[e];
-            wsum[j] = s;
-        }
+    int64_t lo = 0, hi = nu;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (ukey[mid] < key) lo = mid + 1;
+        else hi = mid;
     }
-    if (c) atomicAdd(ndang, c);
+    return lo;
 }
 
-// F += sign * d H_j P[:, j] for every touched column j (one warp per node).
-__global__ void k_inject(const uint8_t *touched, const Off *rp, const int32_t *col, const double *w,
-                         const double *wsum, const double *H, int64_t n, double sd, double *F)
+// A changed row: merge its old links with its batch entries (both sorted by
+// target).  Also W_j of the new row (left to right) and the dangling change.
+__global__ void k_merge_rows(const uint32_t *tlist, int64_t nt, const Off *rp, const int32_t *col, const double *w,
+                             const Off *nrp, const uint64_t *ukey, const uint8_t *eff, const double *uw, int64_t nu,
+                             int32_t *ncol, double *nw, double *nwsum, long long *ddang)
 {
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    long long dd = 0;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nt;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t j = tlist[k];
+        int64_t q = lower_key(ukey, nu, (uint64_t)j << 32);
+        const int64_t qe = lower_key(ukey, nu, (uint64_t)(j + 1) << 32);
+        Off i = rp[j];
+        const Off b = rp[j + 1];
+        Off out = nrp[j];
+        double ws = 0.0;
+        bool first = true;
+        while (i < b || q < qe) {
+            const int64_t to = i < b ? (int64_t)col[i] : INT64_MAX;
+            const int64_t tb = q < qe ? (int64_t)(uint32_t)ukey[q] : INT64_MAX;
+            int32_t c = -1;
+            double x = 1.0;
+            if (to < tb) {
+                c = (int32_t)to;
+                x = w ? w[i] : 1.0;
+                i++;
+            } else if (to == tb) {
+                const unsigned char e = eff[q];
+                if (e != EFF_DEL) {
+                    c = (int32_t)to;
+                    x = e == EFF_UPD ? uw[q] : (w ? w[i] : 1.0);
+                }
+                i++;
+                q++;
+            } else {
+                if (eff[q] == EFF_INS) {
+                    c = (int32_t)tb;
+                    x = uw[q];
+                }
+                q++;
+            }
+            if (c >= 0) {
+                ncol[out] = c;
+                if (nw) {
+                    nw[out] = x;
+                    ws = first ? x : ws + x;
+                    first = false;
+                }
+                out++;
+            }
+        }
+        if (nwsum) nwsum[j] = ws;
+        const bool was = rp[j + 1] == rp[j], now = nrp[j + 1] == nrp[j];
+        dd += (long long)now - (long long)was;
+    }
+    if (dd) atomicAdd((unsigned long long *)ddang, (unsigned long long)dd);
+}
+
+// F += sign * d H_j P[:, j] for the listed columns (one warp per column).
+__global__ void k_inject_list(const uint32_t *tlist, int64_t nt, const Off *rp, const int32_t *col, const double *w,
+                              const double *wsum, const double *H, double sd, double *F)
+{
     const int lane = threadIdx.x & 31;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t j = warp; j < n; j += nwarps) {
-        if (!touched[j]) continue;
+    const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < nt; k += nwarp) {
+        const uint32_t j = tlist[k];
         const Off a = rp[j], b = rp[j + 1];
         if (a == b) continue;
         const double h = sd * H[j];
@@ -167,8 +267,7 @@ di_status update_edges(di_graph_s *g, di_state_s *st, int64_t m, const int32_t *
                        const double *wb, const int8_t *op, cudaStream_t s)
 {
     const int64_t n = g->n, nnz = g->nnz;
-    const int64_t tot = nnz + m;
-    if (tot >= (int64_t(1) << 32)) return DI_ERR_INVALID_ARG;
+    if (nnz + m >= (int64_t(1) << 32)) return DI_ERR_INVALID_ARG;
     Temps t(s);
     unsigned *err;
     DI_TRY(t.get(&err, 1));
@@ -181,76 +280,106 @@ di_status update_edges(di_graph_s *g, di_state_s *st, int64_t m, const int32_t *
     if (herr) return DI_ERR_INVALID_ARG;
     if (m == 0) return DI_OK;
 
+    // 1. the batch alone, sorted by (source, target), batch order kept for ties
     uint64_t *keys, *keys2, *pos, *total;
     uint32_t *vals, *vals2;
-    uint8_t *keep, *touched;
-    double *nw;
-    DI_TRY(t.get(&keys, tot));
-    DI_TRY(t.get(&keys2, tot));
-    DI_TRY(t.get(&vals, tot));
-    DI_TRY(t.get(&vals2, tot));
-    DI_TRY(t.get(&keep, tot));
-    DI_TRY(t.get(&pos, tot));
+    uint8_t *keep;
+    DI_TRY(t.get(&keys, m));
+    DI_TRY(t.get(&keys2, m));
+    DI_TRY(t.get(&vals, m));
+    DI_TRY(t.get(&vals2, m));
+    DI_TRY(t.get(&keep, m));
+    DI_TRY(t.get(&pos, m));
     DI_TRY(t.get(&total, 1));
-    DI_TRY(t.get(&nw, tot));
-    DI_TRY(t.get(&touched, n));
-    DI_CUDA(cudaMemsetAsync(touched, 0, n, s));
-    const Off *rp = static_cast<const Off *>(g->rp);
-    k_keys_old<<<grid_for(n * 32, 256), 256, 0, s>>>(rp, g->col, n, keys, vals);
+    k_batch_keys<<<grid_for(m, 256), 256, 0, s>>>(src, dst, m, keys, vals);
     count_launches(1);
-    k_keys_batch<<<grid_for(m, 256), 256, 0, s>>>(src, dst, m, nnz, keys, vals);
-    count_launches(1);
-    const int b = bits_for(n);
+    const int bb = bits_for(n);
     int lo[16], cnt[16], np = 0;
-    for (int x = 0; x < b; x += 8) { lo[np] = x; cnt[np] = b - x < 8 ? b - x : 8; np++; }
-    for (int x = 0; x < b; x += 8) { lo[np] = 32 + x; cnt[np] = b - x < 8 ? b - x : 8; np++; }
-    DI_TRY(radix_sort_pairs(&keys, &vals, &keys2, &vals2, tot, lo, cnt, np, s));
-    k_resolve<<<grid_for(tot, 256), 256, 0, s>>>(keys, vals, tot, nnz, g->w, g->weighted ? wb : nullptr,
-                                                 op, keep, nw, touched);
+    for (int x = 0; x < bb; x += 8) { lo[np] = x; cnt[np] = bb - x < 8 ? bb - x : 8; np++; }
+    for (int x = 0; x < bb; x += 8) { lo[np] = 32 + x; cnt[np] = bb - x < 8 ? bb - x : 8; np++; }
+    DI_TRY(radix_sort_pairs(&keys, &vals, &keys2, &vals2, m, lo, cnt, np, s));
+    // 2. one entry per distinct link: the last operation on it
+    k_run_ends<<<grid_for(m, 256), 256, 0, s>>>(keys, m, keep);
     count_launches(1);
-    DI_TRY(scan_exclusive<uint8_t>(keep, pos, tot, total, s));
+    DI_TRY(scan_exclusive<uint8_t>(keep, pos, m, total, s));
+    uint64_t nu = 0;
+    DI_CUDA(cudaMemcpyAsync(&nu, total, sizeof(nu), cudaMemcpyDeviceToHost, s));
+    DI_CUDA(cudaStreamSynchronize(s));
+    uint64_t *ukey;
+    int8_t *uop;
+    double *uw;
+    uint8_t *eff, *touched;
+    int *delta;
+    DI_TRY(t.get(&ukey, nu));
+    DI_TRY(t.get(&uop, nu));
+    DI_TRY(t.get(&uw, nu));
+    DI_TRY(t.get(&eff, nu));
+    DI_TRY(t.get(&touched, n));
+    DI_TRY(t.get(&delta, n));
+    DI_CUDA(cudaMemsetAsync(touched, 0, n, s));
+    DI_CUDA(cudaMemsetAsync(delta, 0, sizeof(int) * n, s));
+    k_unique<<<grid_for(m, 256), 256, 0, s>>>(keys, vals, keep, pos, m, op, g->weighted ? wb : nullptr, ukey, uop,
+                                              uw);
+    count_launches(1);
+    // 3. classify against the old rows
+    const Off *rp = static_cast<const Off *>(g->rp);
+    k_classify<<<grid_for((int64_t)nu, 256), 256, 0, s>>>(ukey, uop, uw, (int64_t)nu, rp, g->col, g->w, eff, delta,
+                                                          touched, g->indeg);
+    count_launches(1);
+    // 4. new row pointers
+    uint32_t *deg;
+    uint64_t *ex;
+    DI_TRY(t.get(&deg, n));
+    DI_TRY(t.get(&ex, n));
+    k_new_degree<<<grid_for(n, 256), 256, 0, s>>>(rp, delta, n, deg);
+    count_launches(1);
+    DI_TRY(scan_exclusive<uint32_t>(deg, ex, n, total, s));
     uint64_t mnew = 0;
     DI_CUDA(cudaMemcpyAsync(&mnew, total, sizeof(mnew), cudaMemcpyDeviceToHost, s));
     DI_CUDA(cudaStreamSynchronize(s));
-
-    // new canonical structure
     int32_t *ncol = nullptr;
     double *nwv = nullptr, *nwsum = nullptr;
-    uint32_t *nrp = nullptr, *rows = nullptr;
-    DI_TRY(t.get(&rows, mnew));
+    Off *nrp = nullptr;
     DI_TRY(dalloc_t(&ncol, mnew, s));
     DI_TRY(dalloc_t(&nrp, n + 1, s));
     if (g->weighted) {
         DI_TRY(dalloc_t(&nwv, mnew, s));
         DI_TRY(dalloc_t(&nwsum, n, s));
+        DI_CUDA(cudaMemcpyAsync(nwsum, g->wsum, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
     }
-    k_compact_new<<<grid_for(tot, 256), 256, 0, s>>>(keys, keep, pos, tot, nw, ncol, rows, nwv);
+    k_rp_from_scan<<<grid_for(n + 1, 256), 256, 0, s>>>(ex, total, n, nrp);
     count_launches(1);
-    if (mnew == 0) {
-        k_zero_u32<<<grid_for(n + 1, 256), 256, 0, s>>>(nrp, n + 1);
-        count_launches(1);
-    } else {
-        k_row_ptr_u<uint32_t><<<grid_for(mnew, 256), 256, 0, s>>>(rows, (int64_t)mnew, n, nrp);
-        count_launches(1);
-    }
-    unsigned long long *ndang;
-    DI_TRY(t.get(&ndang, 1));
-    DI_CUDA(cudaMemsetAsync(ndang, 0, sizeof(unsigned long long), s));
-    k_row_sums_u<<<grid_for(n, 256), 256, 0, s>>>(nrp, nwv, n, nwsum, ndang);
+    // 5. unchanged rows move, changed rows are merged
+    k_copy_rows<<<grid_for(n, 256), 256, 0, s>>>(rp, nrp, g->col, g->w, touched, n, ncol, nwv);
     count_launches(1);
-
-    // F += d (P' - P) H: withdraw the old columns, inject the new ones
-    if (st) {
-        k_inject<<<grid_for(n * 32, 256), 256, 0, s>>>(touched, rp, g->col, g->w, g->wsum, st->H, n,
-                                                       -st->d, st->F);
+    uint64_t *tpos;
+    DI_TRY(t.get(&tpos, n));
+    DI_TRY(scan_exclusive<uint8_t>(touched, tpos, n, total, s));
+    uint64_t nt = 0;
+    DI_CUDA(cudaMemcpyAsync(&nt, total, sizeof(nt), cudaMemcpyDeviceToHost, s));
+    DI_CUDA(cudaStreamSynchronize(s));
+    uint32_t *tlist;
+    long long *ddang;
+    DI_TRY(t.get(&tlist, nt));
+    DI_TRY(t.get(&ddang, 1));
+    DI_CUDA(cudaMemsetAsync(ddang, 0, sizeof(long long), s));
+    k_list<<<grid_for(n, 256), 256, 0, s>>>(touched, tpos, n, tlist);
+    count_launches(1);
+    k_merge_rows<<<grid_for((int64_t)nt, 128), 128, 0, s>>>(tlist, (int64_t)nt, rp, g->col, g->w, nrp, ukey, eff,
+                                                            uw, (int64_t)nu, ncol, nwv, nwsum, ddang);
+    count_launches(1);
+    // 6. F += d (P' - P) H: withdraw the old columns, inject the new ones
+    if (st && nt) {
+        k_inject_list<<<grid_for((int64_t)nt * 32, 256), 256, 0, s>>>(tlist, (int64_t)nt, rp, g->col, g->w, g->wsum,
+                                                                      st->H, -st->d, st->F);
         count_launches(1);
-        k_inject<<<grid_for(n * 32, 256), 256, 0, s>>>(touched, nrp, ncol, nwv, nwsum, st->H, n, st->d,
-                                                       st->F);
+        k_inject_list<<<grid_for((int64_t)nt * 32, 256), 256, 0, s>>>(tlist, (int64_t)nt, nrp, ncol, nwv, nwsum,
+                                                                      st->H, st->d, st->F);
         count_launches(1);
     }
     DI_CUDA(cudaGetLastError());
-    unsigned long long hd = 0;
-    DI_CUDA(cudaMemcpyAsync(&hd, ndang, sizeof(hd), cudaMemcpyDeviceToHost, s));
+    long long hd = 0;
+    DI_CUDA(cudaMemcpyAsync(&hd, ddang, sizeof(hd), cudaMemcpyDeviceToHost, s));
     DI_CUDA(cudaStreamSynchronize(s));
 
     // install P'
@@ -269,7 +398,7 @@ di_status update_edges(di_graph_s *g, di_state_s *st, int64_t m, const int32_t *
     g->crow = nullptr;
     g->cw = nullptr;
     g->nnz = (int64_t)mnew;
-    g->n_dangling = (int64_t)hd;
+    g->n_dangling += hd;
     DI_CUDA(cudaStreamSynchronize(s));
     return DI_OK;
 }
