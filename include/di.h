@@ -49,6 +49,7 @@ typedef enum {
 enum { DI_LAYOUT_CSR = 0, DI_LAYOUT_CSC = 1 };
 enum { DI_W_NONE = 0, DI_W_F32 = 1, DI_W_F64 = 2 };
 enum { DI_MEM_HOST = 0, DI_MEM_DEVICE = 1 };
+enum { DI_PREC_F64 = 0, DI_PREC_F32 = 1 };
 
 /* Solver options.  Always start from di_opts_default(). */
 typedef struct {
@@ -65,6 +66,19 @@ typedef struct {
                               completed on dangling columns by Z (Section 3.3).      */
     int32_t profile;       /* 1: time every push launch with CUDA events (implies the
                               loop without CUDA graph); fills the push_* fields.     */
+    int32_t precision;     /* arithmetic of the fluid F moved by the sweeps:
+                              DI_PREC_F64: F is FP64 throughout.
+                              DI_PREC_F32: iterative refinement.  The sweeps move an
+                              FP32 copy of F and add every taken fluid, exactly, to an
+                              FP64 accumulator D (the history gained in this cycle).
+                              A cycle ends once the FP32 |F|_1 bound falls below
+                              refine_ratio times its starting value (or below tol/2
+                              of the stop test); then H += D and the FP64 fluid is
+                              replaced by the exact residual F + d P D - D, which
+                              equals (1-d) Z + d P H - H by Eq. HnFn.  The stop test
+                              is applied to that FP64 residual only, so the returned
+                              bound is certified in FP64 whatever the FP32 rounding. */
+    double refine_ratio;   /* DI_PREC_F32 only: 0 < refine_ratio < 1.               */
 } di_opts;
 
 /* Solver report. */
@@ -82,10 +96,12 @@ typedef struct {
     int64_t push_launches;   /* profile: number of push launches timed                      */
     int64_t push_edges;      /* profile: links pushed by those launches                     */
     int64_t push_entries;    /* profile: frontier entries read by those launches            */
+    int64_t refinements;     /* DI_PREC_F32: FP64 refinement passes run by this call         */
+    int64_t refine_links;    /* DI_PREC_F32: links pushed by those passes                    */
 } di_info;
 
 /* Fill *o with the defaults: theta_factor 1, max_sweeps 100000, check_every 8,
-   use_graph 1, normalize 0, profile 0. */
+   use_graph 1, normalize 0, profile 0, precision DI_PREC_F64, refine_ratio 1e-5. */
 void di_opts_default(di_opts *o);
 
 /* Human-readable name of a status code (static storage). */

@@ -27,12 +27,15 @@ DI_W_F32 = 1
 DI_W_F64 = 2
 DI_MEM_HOST = 0
 DI_MEM_DEVICE = 1
+DI_PREC_F64 = 0
+DI_PREC_F32 = 1
 
 
 class di_opts(ctypes.Structure):
     _fields_ = [("theta_factor", ctypes.c_double), ("max_sweeps", ctypes.c_int64),
                 ("check_every", ctypes.c_int32), ("use_graph", ctypes.c_int32),
-                ("normalize", ctypes.c_int32), ("profile", ctypes.c_int32)]
+                ("normalize", ctypes.c_int32), ("profile", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("refine_ratio", ctypes.c_double)]
 
 
 class di_info(ctypes.Structure):
@@ -41,7 +44,8 @@ class di_info(ctypes.Structure):
                 ("sweeps", ctypes.c_int64), ("diffusions", ctypes.c_int64),
                 ("edge_pushes", ctypes.c_int64), ("time_ms", ctypes.c_double),
                 ("push_ms", ctypes.c_double), ("push_launches", ctypes.c_int64),
-                ("push_edges", ctypes.c_int64), ("push_entries", ctypes.c_int64)]
+                ("push_edges", ctypes.c_int64), ("push_entries", ctypes.c_int64),
+                ("refinements", ctypes.c_int64), ("refine_links", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

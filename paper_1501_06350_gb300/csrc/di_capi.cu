@@ -63,6 +63,9 @@ di_status opts_ok(const di_opts *o)
 {
     if (!(o->theta_factor > 0.0 && o->theta_factor <= 1.0)) return DI_ERR_INVALID_ARG;
     if (o->max_sweeps < 1 || o->check_every < 1) return DI_ERR_INVALID_ARG;
+    if (o->precision != DI_PREC_F64 && o->precision != DI_PREC_F32) return DI_ERR_INVALID_ARG;
+    if (o->precision == DI_PREC_F32 && !(o->refine_ratio > 0.0 && o->refine_ratio < 1.0))
+        return DI_ERR_INVALID_ARG;
     return DI_OK;
 }
 
@@ -73,6 +76,10 @@ di_status prepare(di_graph_s *g, di_state_s *st, cudaStream_t s)
     if (st->gexec) {
         cudaGraphExecDestroy(st->gexec);
         st->gexec = nullptr;
+    }
+    if (st->gexec32) {
+        cudaGraphExecDestroy(st->gexec32);
+        st->gexec32 = nullptr;
     }
     st->dscale_d = -1.0;
     DI_TRY(state_prepare_graph(g, st, s));
@@ -103,6 +110,8 @@ void di_opts_default(di_opts *o)
     o->use_graph = 1;
     o->normalize = 0;
     o->profile = 0;
+    o->precision = DI_PREC_F64;
+    o->refine_ratio = 1e-5;
 }
 
 const char *di_status_str(di_status s)

@@ -344,6 +344,13 @@ __global__ void k_pcol(const int32_t *col, int64_t nnz, const int *slot_of, int3
     }
 }
 
+__global__ void k_w32(const double *w, int64_t nnz, float *w32)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz;
+         e += (int64_t)gridDim.x * blockDim.x)
+        w32[e] = (float)w[e];
+}
+
 // Push copy of the link targets: links into the (at most HOT_K) pages with
 // the most in-links are tagged with their slot so that the push can add them
 // up in shared memory first (one global add per CTA and page instead of one
@@ -354,8 +361,15 @@ di_status graph_build_push_targets(di_graph_s *g, cudaStream_t s)
     const int64_t n = g->n, m = g->nnz;
     dfree(g->pcol, s);
     g->pcol = nullptr;
+    dfree(g->w32, s);
+    g->w32 = nullptr;
     if (!g->hot_node) DI_TRY(dalloc_t(&g->hot_node, HOT_K, s));
     DI_TRY(dalloc_t(&g->pcol, m, s));
+    if (g->weighted) {   // link weights for the FP32-fluid push
+        DI_TRY(dalloc_t(&g->w32, m, s));
+        k_w32<<<grid_for(m, 256), 256, 0, s>>>(g->w, m, g->w32);
+        count_launches(1);
+    }
     Temps t(s);
     unsigned *nhot;
     unsigned long long *hist;
@@ -470,10 +484,12 @@ void graph_release(di_graph_s *g)
     dfree(g->crow, s);
     dfree(g->cw, s);
     dfree(g->pcol, s);
+    dfree(g->w32, s);
     dfree(g->hot_node, s);
     dfree(g->indeg, s);
     cudaStreamSynchronize(s);
     g->pcol = nullptr;
+    g->w32 = nullptr;
     g->hot_node = nullptr;
     g->indeg = nullptr;
     g->rp = nullptr;

@@ -101,6 +101,7 @@ struct di_graph_s {
     // push copy of col: links into the HOT_K most linked-to pages carry
     // 0x80000000 | slot instead of the page id (built on demand per version)
     int32_t *pcol = nullptr;  // [nnz]
+    float *w32 = nullptr;     // [nnz] FP32 copy of w for the FP32-fluid push (weighted only)
     unsigned *indeg = nullptr;    // [n] in-links per page, kept current by updates
     int32_t *hot_node = nullptr;  // [HOT_K] page of each hot slot
     int nhot = 0;
@@ -120,7 +121,8 @@ struct DevCtl {
     double theta_factor;
     double final_l1;       // |F|_1 of the final state (FP64, fixed order)
     double final_l;        // sum of H over dangling nodes (final reduction)
-    double pad0;
+    double sweep_stop;     // the sweep loop ends when its |F|_1 bound is at most this
+    double refine_ratio;   // FP32 fluid: each cycle ends at refine_ratio x its starting |F|_1
     unsigned long long diffusions;
     unsigned long long edge_pushes;
     unsigned long long sweep;         // pushes performed by this call
@@ -148,6 +150,13 @@ struct di_state_s {
     int64_t problem_version = -1;  // graph version (H, F) belongs to
     double *F = nullptr;
     double *H = nullptr;
+    // FP32-fluid form: the working fluid, the FP64 sum of the fluid taken at
+    // each node during the current cycle, and the control block of the
+    // refinement pass (allocated on the first FP32 solve)
+    float *F32 = nullptr;
+    double *D = nullptr;
+    DevCtl *rctl = nullptr;
+    DevCtl *host_rctl = nullptr;
     double *dscale = nullptr;      // d / W_j (or d / out(j)) per node, 0 if dangling
     double dscale_d = -1.0;        // damping dscale was built for
     // frontier of the last selection: one bit per selected node that is not a
@@ -170,7 +179,8 @@ struct di_state_s {
     DevCtl *ctl = nullptr;
     DevCtl *host_ctl = nullptr;    // pinned mirror
     // CUDA graph of the sweep loop
-    cudaGraphExec_t gexec = nullptr;
+    cudaGraphExec_t gexec = nullptr;     // FP64 fluid sweep loop
+    cudaGraphExec_t gexec32 = nullptr;   // FP32 fluid sweep loop
     cudaStream_t gstream = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     // per-sweep frontier statistics (links, entries) written by the selection

@@ -262,13 +262,15 @@ __device__ __forceinline__ void loadP(const double *F, int64_t i0, int64_t n, do
 // --------------------------------------------------------------- reduce
 // FP64 |v|_1 (and, with H, l = sum of H_i over dangling i): per-thread order,
 // warp butterfly, warp partials in order, tile partials in a fixed strided
-// order by the last CTA.  Used at the start (threshold, fixed-point scale)
-// and at the end of a solve (reported residual).
-enum { RED_PLAIN = 0, RED_INIT = 1, RED_FINAL = 2 };
+// order by the last CTA.  Used at the start (threshold) and at the end of a
+// solve (reported residual), and after every refinement pass of the FP32
+// form, where it also writes the FP32 copy of the fluid (v32, every slot of
+// the tile, 0 past n) and sets the targets of the next cycle.
+enum { RED_PLAIN = 0, RED_INIT = 1, RED_FINAL = 2, RED_CYCLE = 3 };
 
 __global__ void __launch_bounds__(SEL_THREADS) k_reduce(const double *v, const double *H, const Off *rp,
                                                        int64_t n, int64_t ntiles, double *part_l1,
-                                                       double *part_l, DevCtl *ctl, int mode)
+                                                       double *part_l, DevCtl *ctl, int mode, float *v32)
 {
     __shared__ double sm[SEL_THREADS / 32 + 1];
     __shared__ int s_last;
@@ -277,6 +279,10 @@ __global__ void __launch_bounds__(SEL_THREADS) k_reduce(const double *v, const d
     constexpr int P = SEL_PER_THREAD;
     double f[P];
     loadP<P>(v, i0, n, f);
+    if (v32) {
+        static_assert(P == 4, "one 16-byte store per thread");
+        *reinterpret_cast<float4 *>(v32 + i0) = make_float4((float)f[0], (float)f[1], (float)f[2], (float)f[3]);
+    }
     double a = fabs(f[0]);
 #pragma unroll
     for (int k = 1; k < P; k++) a += fabs(f[k]);
@@ -309,10 +315,25 @@ __global__ void __launch_bounds__(SEL_THREADS) k_reduce(const double *v, const d
     sl = block_sum_det<SEL_THREADS>(sl, sm);
     if (threadIdx.x == 0) {
         ctl->ticket2 = 0;
-        if (mode == RED_INIT) {
+        if (mode == RED_INIT || mode == RED_CYCLE) {
+            // a loop that ended in its stop test leaves the hubs of its last
+            // selection listed (nobody took them): start the next one clean
+            ctl->nhub = 0;
+            ctl->npieces = 0;
+            ctl->push_ready = 0;
             ctl->l1 = sa;
             ctl->theta = ctl->theta_factor * sa / (double)n;
-            ctl->done = sa <= ctl->stop_l1 ? 1u : 0u;
+            if (mode == RED_INIT) {
+                ctl->sweep_stop = ctl->stop_l1;
+                ctl->done = sa <= ctl->stop_l1 ? 1u : 0u;
+            } else {
+                // FP32 cycle: run to refine_ratio x the exact |F|_1 (never
+                // further than half the final target); a reached sweep cap
+                // stays reached
+                const double target = ctl->refine_ratio * sa;
+                ctl->sweep_stop = target > 0.5 * ctl->stop_l1 ? target : 0.5 * ctl->stop_l1;
+                if (ctl->done != 2u) ctl->done = sa <= ctl->stop_l1 ? 1u : 0u;
+            }
         } else {
             ctl->final_l1 = sa;
             ctl->final_l = sl;
@@ -320,15 +341,88 @@ __global__ void __launch_bounds__(SEL_THREADS) k_reduce(const double *v, const d
     }
 }
 
+// ------------------------------------------------------ fluid word types
+// The sweep kernels move the fluid either as FP64 (the plain form) or as FP32
+// (the iterative-refinement form); these overloads give the raw-word access
+// to either.
+template <typename T>
+struct FluidWord;
+template <>
+struct FluidWord<double> {
+    typedef unsigned long long U;
+    static constexpr unsigned long long ABS = ABS_MASK;
+};
+template <>
+struct FluidWord<float> {
+    typedef unsigned U;
+    static constexpr unsigned ABS = 0x7fffffffu;
+};
+
+__device__ __forceinline__ double word_val(unsigned long long b) { return __longlong_as_double((long long)b); }
+__device__ __forceinline__ float word_val(unsigned b) { return __uint_as_float(b); }
+
+__device__ __forceinline__ unsigned ld_b32(const float *a, unsigned long long pol)
+{
+    unsigned r;
+    asm volatile("ld.global.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(r) : "l"(a), "l"(pol));
+    return r;
+}
+__device__ __forceinline__ unsigned long long ld_word(const double *a, unsigned long long pol) { return ld_b64(a, pol); }
+__device__ __forceinline__ unsigned ld_word(const float *a, unsigned long long pol) { return ld_b32(a, pol); }
+__device__ __forceinline__ void st_word(double *a, unsigned long long v, unsigned long long pol) { st_b64(a, v, pol); }
+__device__ __forceinline__ void st_word(float *a, unsigned v, unsigned long long pol)
+{
+    asm volatile("st.global.L2::cache_hint.b32 [%0], %1, %2;" ::"l"(a), "r"(v), "l"(pol) : "memory");
+}
+
+// The 4 consecutive fluid words of a selection thread (0 past the end).
+__device__ __forceinline__ void load4_keep(const double *F, int64_t i0, int64_t n, unsigned long long *fb,
+                                           unsigned long long pol)
+{
+    loadP_keep<4>(F, i0, n, fb, pol);
+}
+__device__ __forceinline__ void load4_keep(const float *F, int64_t i0, int64_t n, unsigned *fb,
+                                           unsigned long long pol)
+{
+    if (i0 + 3 < n) {
+        asm volatile("ld.global.L2::cache_hint.v4.b32 {%0, %1, %2, %3}, [%4], %5;"
+                     : "=r"(fb[0]), "=r"(fb[1]), "=r"(fb[2]), "=r"(fb[3])
+                     : "l"(F + i0), "l"(pol));
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; k++) fb[k] = (i0 + k < n) ? ld_b32(F + i0 + k, pol) : 0u;
+    }
+}
+
+// |x| as FP32 bits rounded upward / downward (exact for FP32 fluid).
+__device__ __forceinline__ unsigned up32(unsigned long long b) { return f32_up_bits(b); }
+__device__ __forceinline__ unsigned up32(unsigned b) { return b; }
+__device__ __forceinline__ unsigned down32(unsigned long long b) { return f32_down_bits(b); }
+__device__ __forceinline__ unsigned down32(unsigned b) { return b; }
+
+// Bits of the smallest fluid magnitude that passes |F_i| >= theta: for FP32
+// fluid, theta rounded up to the next FP32 value (subnormals included), so
+// that the test on FP32 words is the exact test against the FP64 theta.
+__device__ __forceinline__ unsigned long long theta_word(double th, const double *) { return abs_bits(th); }
+__device__ __forceinline__ unsigned theta_word(double th, const float *)
+{
+    const unsigned long long b = abs_bits(th);
+    if (b < (0x381ull << 52)) return (unsigned)ceil(__longlong_as_double((long long)b) * 0x1p149);
+    return f32_up_bits(b);
+}
+
 // --------------------------------------------------------------- select
+template <typename T>
 __global__ void __launch_bounds__(SEL_THREADS)
-    k_select(const double *F, int64_t n, unsigned *mask, const unsigned *__restrict__ hubbits,
+    k_select(const T *F, int64_t n, unsigned *mask, const unsigned *__restrict__ hubbits,
              unsigned *hub_list, unsigned *tile_cnt, unsigned *tile_diff, float *tile_l1f, unsigned *tile_maxf,
              DevCtl *ctl, int use_cond, cudaGraphConditionalHandle cond,
              int32_t *sel_ids)
 {
+    typedef typename FluidWord<T>::U U;
     constexpr int P = SEL_PER_THREAD;
     constexpr int NW = SEL_THREADS / 32;
+    static_assert(P == 4, "selection threads read 4 consecutive fluid words");
     static_assert(32 % P == 0, "a mask word must cover whole threads");
     __shared__ float s_fx[NW];
     __shared__ unsigned s_mx[NW], s_cnt[NW];
@@ -344,24 +438,24 @@ __global__ void __launch_bounds__(SEL_THREADS)
         return;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) vc->npieces = 0;   // the last push is over
-    const unsigned long long tb = abs_bits(vc->theta);
+    const U tb = theta_word(vc->theta, F);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t tile = blockIdx.x;
     const int64_t i0 = tile * TILE + (int64_t)threadIdx.x * P;
     const unsigned long long keep = pol_last();
 
-    unsigned long long fb[P];
-    loadP_keep<P>(F, i0, n, fb, keep);
+    U fb[P];
+    load4_keep(F, i0, n, fb, keep);
     const unsigned hubw = (__ldg(hubbits + i0 / 32) >> (i0 % 32)) & ((1u << P) - 1u);
     float fx = 0.0f;
     unsigned selm = 0;
     unsigned mb = 0;
 #pragma unroll
     for (int k = 0; k < P; k++) {
-        const unsigned long long b = fb[k] & ABS_MASK;
-        fx = __fadd_ru(fx, __uint_as_float(f32_up_bits(b)));
+        const U b = fb[k] & FluidWord<T>::ABS;
+        fx = __fadd_ru(fx, __uint_as_float(up32(b)));
         if ((i0 + k < n) && b != 0 && b >= tb) selm |= 1u << k;
-        const unsigned md = f32_down_bits(b);
+        const unsigned md = down32(b);
         mb = md > mb ? md : mb;
     }
     const unsigned bits = selm & ~hubw;   // taken by the push
@@ -434,15 +528,23 @@ __global__ void __launch_bounds__(SEL_THREADS)
 
 // ----------------------------------------------------------------- plan
 // Every CTA sums the tile partials; CTA 0 updates the control block.  Then
-// the selected hubs are taken (F is not being written by anyone here) and
-// their rows cut into pieces for the push.
+// the selected hubs are taken (no push is running, so nobody else writes the
+// fluid) and their rows cut into pieces for the push.
+//
+// Ft is the array the fluid is taken from, Fd the array pushes land in, Hs
+// the FP64 array the taken fluid is added to.  A sweep has Ft = Fd (F, or the
+// FP32 fluid) and Hs = H (or the cycle accumulator D).  The refinement pass
+// (SUB) takes from D, adds to H, and lands in the FP64 fluid F, from which it
+// also subtracts the taken amount: F + d P D - D.
+template <typename T, bool SUB>
 __global__ void __launch_bounds__(SEL_THREADS)
-    k_plan(double *F, double *H, const Off *__restrict__ rp, const double *__restrict__ dscale, int64_t n,
+    k_plan(T *Ft, T *Fd, double *Hs, const Off *__restrict__ rp, const double *__restrict__ dscale, int64_t n,
            int64_t ntiles, const unsigned *__restrict__ hub_list, Off *pc_row, Off *pc_len, double *pc_val,
            const unsigned *tile_cnt, const unsigned *tile_diff, const float *tile_l1f,
            const unsigned *tile_maxf, DevCtl *ctl, int use_cond, cudaGraphConditionalHandle cond,
            unsigned long long *stats)
 {
+    typedef typename FluidWord<T>::U U;
     constexpr int NW = SEL_THREADS / 32;
     __shared__ unsigned long long s_red[3][NW];
     __shared__ float s_l1[NW];
@@ -489,7 +591,7 @@ __global__ void __launch_bounds__(SEL_THREADS)
         const unsigned long long sweep = vc->sweep;
         unsigned done = 0;
         // every |F_i| and every partial sum was rounded up: an upper bound of |F_t|_1
-        if (sa <= vc->stop_l1) done = 1;
+        if (sa <= vc->sweep_stop) done = 1;
         else if (sweep >= vc->max_sweeps) done = 2;
         s_go = done == 0;
         if (blockIdx.x == 0) {
@@ -525,13 +627,14 @@ __global__ void __launch_bounds__(SEL_THREADS)
     for (unsigned long long h = (unsigned long long)blockIdx.x * SEL_THREADS + threadIdx.x; h < nhub;
          h += (unsigned long long)gridDim.x * SEL_THREADS) {
         const unsigned i = hub_list[h];
-        const unsigned long long fbits = ld_b64(F + i, keep);
+        const U fbits = ld_word(Ft + i, keep);
         const Off r0 = ldnc_u32(rp + i, stream), r1 = ldnc_u32(rp + i + 1, stream);
-        const unsigned long long hb = ld_b64(H + i, stream);
+        const unsigned long long hb = ld_b64(Hs + i, stream);
         const double ds = ldnc_f64(dscale + i, stream);
-        const double f = __longlong_as_double((long long)fbits);
-        st_b64(H + i, (unsigned long long)__double_as_longlong(__longlong_as_double((long long)hb) + f), stream);
-        st_b64(F + i, 0ull, keep);
+        const double f = (double)word_val(fbits);
+        st_b64(Hs + i, (unsigned long long)__double_as_longlong(__longlong_as_double((long long)hb) + f), stream);
+        st_word(Ft + i, (U)0, keep);
+        if (SUB) red_add_f64(reinterpret_cast<double *>(Fd) + i, -f, keep);
         const Off deg = r1 - r0;
         const double v = f * ds;
         const unsigned np = (deg + PIECE - 1) / PIECE;
@@ -546,50 +649,107 @@ __global__ void __launch_bounds__(SEL_THREADS)
 }
 
 // ----------------------------------------------------------------- push
-__device__ __forceinline__ unsigned long long atom_exch_b64(double *a, unsigned long long v,
-                                                            unsigned long long pol)
+__device__ __forceinline__ unsigned long long atom_exch_word(double *a, unsigned long long pol)
 {
     unsigned long long old;
     asm volatile("atom.global.exch.L2::cache_hint.b64 %0, [%1], %2, %3;"
                  : "=l"(old)
-                 : "l"(a), "l"(v), "l"(pol)
+                 : "l"(a), "l"(0ull), "l"(pol)
                  : "memory");
     return old;
+}
+__device__ __forceinline__ unsigned atom_exch_word(float *a, unsigned long long pol)
+{
+    unsigned old;
+    asm volatile("atom.global.exch.L2::cache_hint.b32 %0, [%1], %2, %3;"
+                 : "=r"(old)
+                 : "l"(a), "r"(0u), "l"(pol)
+                 : "memory");
+    return old;
+}
+__device__ __forceinline__ void red_add(double *a, double v, unsigned long long pol) { red_add_f64(a, v, pol); }
+__device__ __forceinline__ void red_add(float *a, float v, unsigned long long pol)
+{
+    asm volatile("red.global.add.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(a), "f"(v), "l"(pol) : "memory");
+}
+__device__ __forceinline__ float ldnc_f32(const float *a, unsigned long long pol)
+{
+    unsigned r;
+    asm volatile("ld.global.nc.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(r) : "l"(a), "l"(pol));
+    return __uint_as_float(r);
+}
+
+// Per-link value of a weighted push: the node's share times the link weight
+// (FP64 weights for FP64 fluid, the FP32 copy for FP32 fluid).
+__device__ __forceinline__ double link_weight(const double *w, const float *, Off link, unsigned long long pol)
+{
+    return ldnc_f64(w + link, pol);
+}
+__device__ __forceinline__ float link_weight(const float *w32, Off link, unsigned long long pol)
+{
+    return ldnc_f32(w32 + link, pol);
+}
+
+// Shared-memory accumulation for the hot pages: FP64 contributions as 64-bit
+// fixed point (native integer atomics; the shared FP64 add is not native),
+// FP32 contributions with the native shared FP32 add.
+__device__ __forceinline__ void hot_add(unsigned long long *s_hot, int slot, double v, int hot_shift)
+{
+    atomicAdd(s_hot + slot, (unsigned long long)to_fixed64(v, hot_shift));
+}
+__device__ __forceinline__ void hot_add(unsigned long long *s_hot, int slot, float v, int)
+{
+    atomicAdd(reinterpret_cast<float *>(s_hot) + slot, v);
+}
+__device__ __forceinline__ void hot_flush(double *Fd, const int32_t *hot_node, const unsigned long long *s_hot,
+                                          int k, int hot_shift, unsigned long long keep)
+{
+    const long long a = (long long)s_hot[k];
+    if (a != 0) red_add_f64(Fd + __ldg(hot_node + k), scalbn((double)a, -hot_shift), keep);
+}
+__device__ __forceinline__ void hot_flush(float *Fd, const int32_t *hot_node, const unsigned long long *s_hot,
+                                          int k, int, unsigned long long keep)
+{
+    const float a = reinterpret_cast<const float *>(s_hot)[k];
+    if (a != 0.0f) red_add(Fd + __ldg(hot_node + k), a, keep);
 }
 
 // Scatter helper: 4 x 32 links in flight per warp.  lane_link(e) gives the
 // link and the value for the warp's e-th link (e < total).  Targets tagged
 // in the push copy of the links (hot pages) are added in shared memory.
-template <bool WEIGHTED, typename LinkOf>
+template <typename T, bool WEIGHTED, typename LinkOf>
 __device__ __forceinline__ void scatter_links(unsigned total, LinkOf lane_link, const int32_t *pcol,
-                                              const double *w, double *F, unsigned long long *s_hot,
-                                              int hot_shift, unsigned long long keep,
+                                              const double *w, const float *w32, T *Fd,
+                                              unsigned long long *s_hot, int hot_shift, unsigned long long keep,
                                               unsigned long long stream)
 {
     const int lane = threadIdx.x & 31;
     for (unsigned base = 0; base < total; base += 128) {
         int32_t c[4];
-        double v[4];
+        T v[4];
         bool ok[4];
 #pragma unroll
         for (int g = 0; g < 4; g++) {
             const unsigned e = base + (unsigned)(g * 32 + lane);
             Off link;
-            double vj;
+            T vj;
             lane_link(e < total ? e : total - 1, link, vj);
             ok[g] = e < total;
             c[g] = 0;
             v[g] = vj;
             if (ok[g]) {
                 c[g] = ldnc_s32(pcol + link, stream);
-                if (WEIGHTED) v[g] = vj * ldnc_f64(w + link, stream);
+                if (WEIGHTED) {
+                    if constexpr (sizeof(T) == 8) v[g] = vj * link_weight(w, w32, link, stream);
+                    else v[g] = vj * link_weight(w32, link, stream);
+                }
             }
         }
 #pragma unroll
         for (int g = 0; g < 4; g++) {
             if (!ok[g]) continue;
-            if (c[g] >= 0) red_add_f64(F + c[g], v[g], keep);
-            else atomicAdd(s_hot + (c[g] & 0x7fffffff), (unsigned long long)to_fixed64(v[g], hot_shift));
+            if (c[g] >= 0) red_add(Fd + c[g], v[g], keep);
+            else hot_add(s_hot, c[g] & 0x7fffffff, v[g], hot_shift);
         }
     }
 }
@@ -600,24 +760,27 @@ __device__ __forceinline__ void scatter_links(unsigned total, LinkOf lane_link, 
 // and loads of a unit are issued before any is used.  The taken nodes' links
 // are enumerated 32 at a time; a link finds its lane by a binary search over
 // the lanes' exclusive link prefixes (shuffles) and its node among the lane's
-// four by their running degrees.
-template <bool WEIGHTED>
+// four by their running degrees.  Ft / Fd / Hs / SUB as for k_plan.
+template <typename T, bool WEIGHTED, bool SUB>
 __global__ void __launch_bounds__(PUSH_THREADS)
-    k_push(double *F, double *H, const Off *__restrict__ rp, const double *__restrict__ dscale,
+    k_push(T *Ft, T *Fd, double *Hs, const Off *__restrict__ rp, const double *__restrict__ dscale,
            const unsigned *__restrict__ mask, const Off *__restrict__ pc_row, const Off *__restrict__ pc_len,
            const double *__restrict__ pc_val, int64_t ngroups, const int32_t *__restrict__ pcol,
-           const int32_t *__restrict__ hot_node, int nhot, const double *__restrict__ w, DevCtl *ctl)
+           const int32_t *__restrict__ hot_node, int nhot, const double *__restrict__ w,
+           const float *__restrict__ w32, DevCtl *ctl)
 {
+    typedef typename FluidWord<T>::U U;
     constexpr int Q = 4;
     __shared__ unsigned long long s_links[PUSH_THREADS / 32];
-    __shared__ unsigned long long s_hot[HOT_K];   // fixed point, units of 2^-hot_shift
+    __shared__ unsigned long long s_hot[HOT_K];   // FP64: fixed point, units of 2^-hot_shift; FP32: floats
     volatile DevCtl *vc = ctl;
     if (!vc->push_ready) return;
     // Fluid taken twice in one sweep (pushed in, then taken again) is counted
     // twice, so the values pushed in a sweep add up to at most
     // d |F|_1 / (1 - d) < 8 |F|_1 < 2^(e+3) in magnitude for d <= 7/8, and
     // for larger d the sum of any one CTA's share stays far below that:
-    // 2^(58 - e) keeps every slot below 2^61.
+    // 2^(58 - e) keeps every slot below 2^61.  (The refinement pass takes
+    // each node once: its pushes add up to at most d |D|_1 < |D|_1.)
     int e = 0;
     frexp(vc->l1, &e);
     const int hot_shift = 58 - e;
@@ -641,20 +804,21 @@ __global__ void __launch_bounds__(PUSH_THREADS)
             if (!__any_sync(FULL, bits)) continue;
             const unsigned long long i0 = u * (32 * Q) + (unsigned long long)lane * Q;
             Off r[Q + 1];
-            double val[Q];
+            T val[Q];
             unsigned c1 = 0, c2 = 0, c3 = 0, tot = 0;
             if (bits) {
-                unsigned long long fb[Q], hb[Q];
+                U fb[Q];
+                unsigned long long hb[Q];
                 double ds[Q];
 #pragma unroll
                 for (int k = 0; k < Q; k++) {
-                    fb[k] = 0ull;
+                    fb[k] = 0;
                     hb[k] = 0ull;
                     ds[k] = 0.0;
                     if (!((bits >> k) & 1u)) continue;
                     // take (Eq. defF): whatever fluid the node holds now
-                    fb[k] = atom_exch_b64(F + i0 + k, 0ull, keep);
-                    hb[k] = ld_b64(H + i0 + k, stream);
+                    fb[k] = atom_exch_word(Ft + i0 + k, keep);
+                    hb[k] = ld_b64(Hs + i0 + k, stream);
                     ds[k] = ldnc_f64(dscale + i0 + k, stream);
                 }
 #pragma unroll
@@ -663,14 +827,15 @@ __global__ void __launch_bounds__(PUSH_THREADS)
 #pragma unroll
                 for (int k = 0; k < Q; k++) {
                     dg[k] = 0;
-                    val[k] = 0.0;
+                    val[k] = (T)0;
                     if (!((bits >> k) & 1u)) continue;
-                    const double f = __longlong_as_double((long long)fb[k]);
-                    st_b64(H + i0 + k,
+                    const double f = (double)word_val(fb[k]);
+                    st_b64(Hs + i0 + k,
                            (unsigned long long)__double_as_longlong(__longlong_as_double((long long)hb[k]) + f),
                            stream);
+                    if (SUB) red_add_f64(reinterpret_cast<double *>(Fd) + i0 + k, -f, keep);
                     dg[k] = r[k + 1] - r[k];
-                    val[k] = f * ds[k];
+                    val[k] = (T)(f * ds[k]);
                 }
                 c1 = dg[0];
                 c2 = c1 + dg[1];
@@ -680,7 +845,7 @@ __global__ void __launch_bounds__(PUSH_THREADS)
 #pragma unroll
                 for (int k = 0; k <= Q; k++) r[k] = 0;
 #pragma unroll
-                for (int k = 0; k < Q; k++) val[k] = 0.0;
+                for (int k = 0; k < Q; k++) val[k] = (T)0;
             }
             unsigned incl = tot;
 #pragma unroll
@@ -691,7 +856,7 @@ __global__ void __launch_bounds__(PUSH_THREADS)
             const unsigned total = __shfl_sync(FULL, incl, 31);
             const unsigned excl = incl - tot;
             links += total;
-            auto lane_link = [&](unsigned e, Off &link, double &vj) {
+            auto lane_link = [&](unsigned e, Off &link, T &vj) {
                 int j = 0;
 #pragma unroll
                 for (int step = 16; step > 0; step >>= 1) {
@@ -703,33 +868,30 @@ __global__ void __launch_bounds__(PUSH_THREADS)
                                a3 = __shfl_sync(FULL, c3, j);
                 const Off q0 = __shfl_sync(FULL, r[0], j), q1 = __shfl_sync(FULL, r[1], j),
                           q2 = __shfl_sync(FULL, r[2], j), q3 = __shfl_sync(FULL, r[3], j);
-                const double v0 = __shfl_sync(FULL, val[0], j), v1 = __shfl_sync(FULL, val[1], j),
-                             v2 = __shfl_sync(FULL, val[2], j), v3 = __shfl_sync(FULL, val[3], j);
+                const T v0 = __shfl_sync(FULL, val[0], j), v1 = __shfl_sync(FULL, val[1], j),
+                        v2 = __shfl_sync(FULL, val[2], j), v3 = __shfl_sync(FULL, val[3], j);
                 if (o < a1) { link = q0 + o; vj = v0; }
                 else if (o < a2) { link = q1 + (o - a1); vj = v1; }
                 else if (o < a3) { link = q2 + (o - a2); vj = v2; }
                 else { link = q3 + (o - a3); vj = v3; }
             };
-            scatter_links<WEIGHTED>(total, lane_link, pcol, w, F, s_hot, hot_shift, keep, stream);
+            scatter_links<T, WEIGHTED>(total, lane_link, pcol, w, w32, Fd, s_hot, hot_shift, keep, stream);
         } else {
             const unsigned long long p = u - nunits;
             const Off row = ldnc_u32(pc_row + p, stream), len = ldnc_u32(pc_len + p, stream);
-            const double pv = ldnc_f64(pc_val + p, stream);
+            const T pv = (T)ldnc_f64(pc_val + p, stream);
             links += len;
-            auto piece_link = [&](unsigned e, Off &link, double &vj) {
+            auto piece_link = [&](unsigned e, Off &link, T &vj) {
                 link = row + e;
                 vj = pv;
             };
-            scatter_links<WEIGHTED>(len, piece_link, pcol, w, F, s_hot, hot_shift, keep, stream);
+            scatter_links<T, WEIGHTED>(len, piece_link, pcol, w, w32, Fd, s_hot, hot_shift, keep, stream);
         }
     }
     if (lane == 0) s_links[threadIdx.x >> 5] = links;
     __syncthreads();
     // one global add per hot page this CTA touched
-    for (int k = threadIdx.x; k < nhot; k += PUSH_THREADS) {
-        const long long a = (long long)s_hot[k];
-        if (a != 0) red_add_f64(F + __ldg(hot_node + k), scalbn((double)a, -hot_shift), keep);
-    }
+    for (int k = threadIdx.x; k < nhot; k += PUSH_THREADS) hot_flush(Fd, hot_node, s_hot, k, hot_shift, keep);
     if (threadIdx.x == 0) {
         unsigned long long t = 0;
         for (int q = 0; q < PUSH_THREADS / 32; q++) t += s_links[q];
@@ -764,16 +926,24 @@ static unsigned grid_for(int64_t work, int threads)
     return (unsigned)b;
 }
 
-static int push_grid(int device)
+// Sweep variants: FP64 fluid, FP32 fluid, FP64 refinement pass.
+enum SweepKind { SW_F64 = 0, SW_F32 = 1, SW_REFINE = 2 };
+
+static int push_grid(int device, SweepKind kind, bool weighted)
 {
-    static int cached = 0;
-    if (!cached) {
+    static int cached[3][2];
+    int &c = cached[kind][weighted ? 1 : 0];
+    if (!c) {
         int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_push<false>, PUSH_THREADS, 0);
+        const void *fn = nullptr;
+        if (kind == SW_F32) fn = weighted ? (const void *)k_push<float, true, false> : (const void *)k_push<float, false, false>;
+        else if (kind == SW_REFINE) fn = weighted ? (const void *)k_push<double, true, true> : (const void *)k_push<double, false, true>;
+        else fn = weighted ? (const void *)k_push<double, true, false> : (const void *)k_push<double, false, false>;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, PUSH_THREADS, 0);
         if (per_sm < 1) per_sm = 1;
-        cached = per_sm * sm_count(device);
+        c = per_sm * sm_count(device);
     }
-    return cached;
+    return c;
 }
 
 // Buffers derived from the graph's degrees: static hub bit mask, hub list
@@ -850,12 +1020,14 @@ di_status state_free(di_state_s *st)
 {
     cudaStream_t s = 0;
     if (st->gexec) cudaGraphExecDestroy(st->gexec);
+    if (st->gexec32) cudaGraphExecDestroy(st->gexec32);
     if (st->gstream) cudaStreamDestroy(st->gstream);
     void *bufs[] = {st->F, st->H, st->dscale, st->mask, st->hubbits, st->hub_list, st->pc_row, st->pc_len,
                     st->pc_val, st->tile_cnt, st->tile_diff, st->tile_l1f, st->tile_maxf, st->tile_l1,
-                    st->tile_l, st->ctl, st->stats};
+                    st->tile_l, st->ctl, st->stats, st->F32, st->D, st->rctl};
     for (void *p : bufs) dfree(p, s);
     if (st->host_ctl) cudaFreeHost(st->host_ctl);
+    if (st->host_rctl) cudaFreeHost(st->host_rctl);
     if (st->ev0) cudaEventDestroy(st->ev0);
     if (st->ev1) cudaEventDestroy(st->ev1);
     for (int i = 0; i < st->npev; i++) cudaEventDestroy(st->pev[i]);
@@ -866,45 +1038,88 @@ di_status state_free(di_state_s *st)
     return DI_OK;
 }
 
-static void launch_select(di_graph_s *g, di_state_s *st, cudaStream_t s, int use_cond,
+// The arrays one sweep works on (see k_plan): take from Ft, push into Fd,
+// add the taken fluid to Hs, under control block ctl.
+struct Sweep {
+    SweepKind kind;
+    void *Ft;
+    void *Fd;
+    double *Hs;
+    DevCtl *ctl;
+};
+
+static Sweep sweep_of(di_state_s *st, SweepKind kind)
+{
+    if (kind == SW_F32) return Sweep{kind, st->F32, st->F32, st->D, st->ctl};
+    if (kind == SW_REFINE) return Sweep{kind, st->D, st->F, st->H, st->rctl};
+    return Sweep{kind, st->F, st->F, st->H, st->ctl};
+}
+
+static void launch_select(di_graph_s *g, di_state_s *st, const Sweep &w, cudaStream_t s, int use_cond,
                           cudaGraphConditionalHandle h, int32_t *sel_ids = nullptr)
 {
-    k_select<<<(unsigned)st->ntiles, SEL_THREADS, 0, s>>>(st->F, g->n, st->mask, st->hubbits, st->hub_list,
-                                                          st->tile_cnt, st->tile_diff, st->tile_l1f,
-                                                          st->tile_maxf, st->ctl, use_cond, h, sel_ids);
+    if (w.kind == SW_F32)
+        k_select<float><<<(unsigned)st->ntiles, SEL_THREADS, 0, s>>>(
+            static_cast<const float *>(w.Ft), g->n, st->mask, st->hubbits, st->hub_list, st->tile_cnt,
+            st->tile_diff, st->tile_l1f, st->tile_maxf, w.ctl, use_cond, h, sel_ids);
+    else
+        k_select<double><<<(unsigned)st->ntiles, SEL_THREADS, 0, s>>>(
+            static_cast<const double *>(w.Ft), g->n, st->mask, st->hubbits, st->hub_list, st->tile_cnt,
+            st->tile_diff, st->tile_l1f, st->tile_maxf, w.ctl, use_cond, h, sel_ids);
     count_launches(1);
 }
 
-static void launch_plan(di_graph_s *g, di_state_s *st, cudaStream_t s, int use_cond,
+static void launch_plan(di_graph_s *g, di_state_s *st, const Sweep &w, cudaStream_t s, int use_cond,
                         cudaGraphConditionalHandle h)
 {
-    k_plan<<<PLAN_CTAS, SEL_THREADS, 0, s>>>(st->F, st->H, static_cast<const Off *>(g->rp), st->dscale, g->n,
-                                             st->ntiles, st->hub_list, st->pc_row, st->pc_len, st->pc_val,
-                                             st->tile_cnt, st->tile_diff, st->tile_l1f, st->tile_maxf, st->ctl,
-                                             use_cond, h, st->stats);
+    const Off *rp = static_cast<const Off *>(g->rp);
+    unsigned long long *stats = w.kind == SW_REFINE ? nullptr : st->stats;
+#define DI_PLAN_ARGS                                                                                      \
+    w.Hs, rp, st->dscale, g->n, st->ntiles, st->hub_list, st->pc_row, st->pc_len, st->pc_val, st->tile_cnt, \
+        st->tile_diff, st->tile_l1f, st->tile_maxf, w.ctl, use_cond, h, stats
+    if (w.kind == SW_F32)
+        k_plan<float, false><<<PLAN_CTAS, SEL_THREADS, 0, s>>>(static_cast<float *>(w.Ft),
+                                                               static_cast<float *>(w.Fd), DI_PLAN_ARGS);
+    else if (w.kind == SW_REFINE)
+        k_plan<double, true><<<PLAN_CTAS, SEL_THREADS, 0, s>>>(static_cast<double *>(w.Ft),
+                                                               static_cast<double *>(w.Fd), DI_PLAN_ARGS);
+    else
+        k_plan<double, false><<<PLAN_CTAS, SEL_THREADS, 0, s>>>(static_cast<double *>(w.Ft),
+                                                                static_cast<double *>(w.Fd), DI_PLAN_ARGS);
+#undef DI_PLAN_ARGS
     count_launches(1);
 }
 
-static void launch_push(di_graph_s *g, di_state_s *st, cudaStream_t s)
+static void launch_push(di_graph_s *g, di_state_s *st, const Sweep &w, cudaStream_t s)
 {
-    const int grid = push_grid(st->device);
+    const int grid = push_grid(st->device, w.kind, g->weighted);
     const int64_t ngroups = st->ntiles * TILE / 32;
     const Off *rp = static_cast<const Off *>(g->rp);
-    if (g->weighted)
-        k_push<true><<<grid, PUSH_THREADS, 0, s>>>(st->F, st->H, rp, st->dscale, st->mask, st->pc_row,
-                                                  st->pc_len, st->pc_val, ngroups, g->pcol, g->hot_node,
-                                                  g->nhot, g->w, st->ctl);
-    else
-        k_push<false><<<grid, PUSH_THREADS, 0, s>>>(st->F, st->H, rp, st->dscale, st->mask, st->pc_row,
-                                                   st->pc_len, st->pc_val, ngroups, g->pcol, g->hot_node,
-                                                   g->nhot, nullptr, st->ctl);
+#define DI_PUSH_ARGS                                                                                  \
+    w.Hs, rp, st->dscale, st->mask, st->pc_row, st->pc_len, st->pc_val, ngroups, g->pcol, g->hot_node, \
+        g->nhot, g->w, g->w32, w.ctl
+    float *f32t = static_cast<float *>(w.Ft), *f32d = static_cast<float *>(w.Fd);
+    double *f64t = static_cast<double *>(w.Ft), *f64d = static_cast<double *>(w.Fd);
+    if (w.kind == SW_F32) {
+        if (g->weighted) k_push<float, true, false><<<grid, PUSH_THREADS, 0, s>>>(f32t, f32d, DI_PUSH_ARGS);
+        else k_push<float, false, false><<<grid, PUSH_THREADS, 0, s>>>(f32t, f32d, DI_PUSH_ARGS);
+    } else if (w.kind == SW_REFINE) {
+        if (g->weighted) k_push<double, true, true><<<grid, PUSH_THREADS, 0, s>>>(f64t, f64d, DI_PUSH_ARGS);
+        else k_push<double, false, true><<<grid, PUSH_THREADS, 0, s>>>(f64t, f64d, DI_PUSH_ARGS);
+    } else {
+        if (g->weighted) k_push<double, true, false><<<grid, PUSH_THREADS, 0, s>>>(f64t, f64d, DI_PUSH_ARGS);
+        else k_push<double, false, false><<<grid, PUSH_THREADS, 0, s>>>(f64t, f64d, DI_PUSH_ARGS);
+    }
+#undef DI_PUSH_ARGS
     count_launches(1);
 }
 
-static di_status build_graph_exec(di_graph_s *g, di_state_s *st)
+static di_status build_graph_exec(di_graph_s *g, di_state_s *st, SweepKind kind)
 {
-    if (st->gexec) return DI_OK;
-    (void)push_grid(st->device);  // occupancy query outside the capture
+    cudaGraphExec_t &gx = kind == SW_F32 ? st->gexec32 : st->gexec;
+    if (gx) return DI_OK;
+    const Sweep w = sweep_of(st, kind);
+    (void)push_grid(st->device, kind, g->weighted);  // occupancy query outside the capture
     if (!st->gstream) DI_CUDA(cudaStreamCreateWithFlags(&st->gstream, cudaStreamNonBlocking));
     cudaGraph_t graph;
     DI_CUDA(cudaGraphCreate(&graph, 0));
@@ -929,16 +1144,16 @@ static di_status build_graph_exec(di_graph_s *g, di_state_s *st)
     e = cudaStreamBeginCaptureToGraph(st->gstream, body, nullptr, nullptr, 0,
                                       cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        launch_select(g, st, st->gstream, 1, h);
-        launch_plan(g, st, st->gstream, 1, h);
-        launch_push(g, st, st->gstream);
+        launch_select(g, st, w, st->gstream, 1, h);
+        launch_plan(g, st, w, st->gstream, 1, h);
+        launch_push(g, st, w, st->gstream);
         cudaGraph_t out = nullptr;
         e = cudaStreamEndCapture(st->gstream, &out);
     }
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&st->gexec, graph, 0);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&gx, graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) {
-        st->gexec = nullptr;
+        gx = nullptr;
         return note_cuda(e);
     }
     return DI_OK;
@@ -955,7 +1170,7 @@ di_status l1_device(di_graph_s *g, const double *v, double *out_host, cudaStream
     DI_TRY(t.get(&ctl, 1));
     DI_CUDA(cudaMemsetAsync(ctl, 0, sizeof(DevCtl), s));
     k_reduce<<<(unsigned)ntiles, SEL_THREADS, 0, s>>>(v, nullptr, static_cast<const Off *>(g->rp), g->n,
-                                                      ntiles, p1, p2, ctl, RED_PLAIN);
+                                                      ntiles, p1, p2, ctl, RED_PLAIN, nullptr);
     count_launches(1);
     DI_CUDA(cudaGetLastError());
     DI_CUDA(cudaMemcpyAsync(out_host, &ctl->final_l1, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -971,7 +1186,7 @@ di_status l1_device_into(di_graph_s *g, const double *v, double *part_l1, double
     const int64_t ntiles = (g->n + TILE - 1) / TILE;
     DI_CUDA(cudaMemsetAsync(ctl, 0, sizeof(DevCtl), s));
     k_reduce<<<(unsigned)ntiles, SEL_THREADS, 0, s>>>(v, nullptr, static_cast<const Off *>(g->rp), g->n,
-                                                      ntiles, part_l1, part_l, ctl, RED_PLAIN);
+                                                      ntiles, part_l1, part_l, ctl, RED_PLAIN, nullptr);
     count_launches(1);
     DI_CUDA(cudaGetLastError());
     DI_CUDA(cudaMemcpyAsync(out_host, &ctl->final_l1, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -979,11 +1194,93 @@ di_status l1_device_into(di_graph_s *g, const double *v, double *part_l1, double
     return DI_OK;
 }
 
+// Buffers of the FP32-fluid form, allocated on its first use.
+static di_status state_alloc_f32(di_state_s *st, cudaStream_t s)
+{
+    if (st->F32) return DI_OK;
+    const int64_t slots = st->ntiles * TILE;
+    DI_TRY(dalloc_t(&st->D, slots, s));
+    DI_CUDA(cudaMemsetAsync(st->D, 0, sizeof(double) * slots, s));
+    DI_TRY(dalloc_t(&st->rctl, 1, s));
+    DI_CUDA(cudaMallocHost(reinterpret_cast<void **>(&st->host_rctl), sizeof(DevCtl)));
+    DI_TRY(dalloc_t(&st->F32, slots, s));
+    return DI_OK;
+}
+
+// Sweeps until the control block says done (1 reached its sweep_stop, 2 sweep
+// cap): one CUDA-graph launch, or launches polled every check_every sweeps
+// (with CUDA events around every push when profiling).
+struct PushProfile {
+    int npairs = 0;
+};
+
+static di_status run_sweeps(di_graph_s *g, di_state_s *st, SweepKind kind, const di_opts *o, cudaStream_t s,
+                            PushProfile &pp)
+{
+    const Sweep w = sweep_of(st, kind);
+    DevCtl *hc = st->host_ctl;
+    const bool graph_mode = o->use_graph && !o->profile;
+    if (graph_mode) {
+        DI_TRY(build_graph_exec(g, st, kind));
+        DI_CUDA(cudaGraphLaunch(kind == SW_F32 ? st->gexec32 : st->gexec, s));
+        return DI_OK;
+    }
+    for (;;) {
+        for (int k = 0; k < o->check_every; k++) {
+            launch_select(g, st, w, s, 0, cudaGraphConditionalHandle{});
+            launch_plan(g, st, w, s, 0, cudaGraphConditionalHandle{});
+            if (o->profile && pp.npairs < STAT_CAP) {
+                while (st->npev < 2 * (pp.npairs + 1)) DI_CUDA(cudaEventCreate(&st->pev[st->npev++]));
+                DI_CUDA(cudaEventRecord(st->pev[2 * pp.npairs], s));
+                launch_push(g, st, w, s);
+                DI_CUDA(cudaEventRecord(st->pev[2 * pp.npairs + 1], s));
+                pp.npairs++;
+            } else {
+                launch_push(g, st, w, s);
+            }
+        }
+        DI_CUDA(cudaGetLastError());
+        DI_CUDA(cudaMemcpyAsync(hc, st->ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, s));
+        DI_CUDA(cudaStreamSynchronize(s));
+        if (hc->done) return DI_OK;
+    }
+}
+
+// One refinement pass of the FP32 form: H += D, F += d P D - D, D = 0 (a
+// single sweep of the push machinery over every node with D != 0, into the
+// FP64 fluid), then the exact |F|_1, the FP32 copy of F and the next cycle's
+// targets (k_reduce, RED_CYCLE).
+static di_status refine_pass(di_graph_s *g, di_state_s *st, cudaStream_t s)
+{
+    DevCtl *r = st->host_rctl;
+    memset(r, 0, sizeof(DevCtl));
+    r->theta = 0.0;                 // every node with D != 0
+    r->stop_l1 = -1.0;
+    r->sweep_stop = -1.0;           // one sweep, never "converged"
+    r->theta_factor = 1.0;
+    r->max_sweeps = ~0ull;
+    DI_CUDA(cudaMemcpyAsync(st->rctl, r, sizeof(DevCtl), cudaMemcpyHostToDevice, s));
+    const Sweep w = sweep_of(st, SW_REFINE);
+    launch_select(g, st, w, s, 0, cudaGraphConditionalHandle{});
+    launch_plan(g, st, w, s, 0, cudaGraphConditionalHandle{});
+    launch_push(g, st, w, s);
+    k_reduce<<<(unsigned)st->ntiles, SEL_THREADS, 0, s>>>(st->F, nullptr, static_cast<const Off *>(g->rp), g->n,
+                                                          st->ntiles, st->tile_l1, st->tile_l, st->ctl, RED_CYCLE,
+                                                          st->F32);
+    count_launches(1);
+    DI_CUDA(cudaGetLastError());
+    return DI_OK;
+}
+
+constexpr int MAX_CYCLES = 64;   // FP32-form cycles per call (each gains >= 1/refine_ratio)
+
 di_status solve_loop(di_graph_s *g, di_state_s *st, double tol, const di_opts *o, di_info *info,
                      cudaStream_t s, bool fresh, const double *Z_dev)
 {
     const int64_t n = g->n;
     const double d = st->d;
+    const bool f32 = o->precision == DI_PREC_F32;
+    if (f32) DI_TRY(state_alloc_f32(st, s));
     if (fresh) {
         k_init<<<grid_for(n, 256), 256, 0, s>>>(st->F, st->H, Z_dev, n, 1.0 - d, 1.0 / (double)n);
         count_launches(1);
@@ -999,63 +1296,64 @@ di_status solve_loop(di_graph_s *g, di_state_s *st, double tol, const di_opts *o
     hc->d = d;
     hc->theta_factor = o->theta_factor;
     hc->stop_l1 = (1.0 - d) * tol;
+    hc->refine_ratio = o->refine_ratio;
     hc->max_sweeps = (unsigned long long)o->max_sweeps;
     DI_CUDA(cudaMemcpyAsync(st->ctl, hc, sizeof(DevCtl), cudaMemcpyHostToDevice, s));
     k_reduce<<<(unsigned)st->ntiles, SEL_THREADS, 0, s>>>(st->F, nullptr, static_cast<const Off *>(g->rp),
                                                           n, st->ntiles, st->tile_l1, st->tile_l,
-                                                          st->ctl, RED_INIT);
+                                                          st->ctl, f32 ? RED_CYCLE : RED_INIT,
+                                                          f32 ? st->F32 : nullptr);
     count_launches(1);
     DI_CUDA(cudaGetLastError());
 
     double push_ms = 0.0;
     int64_t push_launches = 0, push_edges = 0, push_entries = 0;
-    const bool graph_mode = o->use_graph && !o->profile;
-    if (graph_mode) DI_TRY(build_graph_exec(g, st));
+    int64_t refinements = 0, refine_links = 0;
     if (o->profile && !st->pev) {
         st->pev = new (std::nothrow) cudaEvent_t[2 * STAT_CAP];
         if (!st->pev) return DI_ERR_OOM;
     }
-    int npairs = 0;
+    PushProfile pp;
     DI_CUDA(cudaEventRecord(st->ev0, s));
-    if (graph_mode) {
-        DI_CUDA(cudaGraphLaunch(st->gexec, s));
+    if (!f32) {
+        DI_TRY(run_sweeps(g, st, SW_F64, o, s, pp));
     } else {
-        for (;;) {
-            for (int k = 0; k < o->check_every; k++) {
-                launch_select(g, st, s, 0, cudaGraphConditionalHandle{});
-                launch_plan(g, st, s, 0, cudaGraphConditionalHandle{});
-                if (o->profile && npairs < STAT_CAP) {
-                    while (st->npev < 2 * (npairs + 1)) DI_CUDA(cudaEventCreate(&st->pev[st->npev++]));
-                    DI_CUDA(cudaEventRecord(st->pev[2 * npairs], s));
-                    launch_push(g, st, s);
-                    DI_CUDA(cudaEventRecord(st->pev[2 * npairs + 1], s));
-                    npairs++;
-                } else {
-                    launch_push(g, st, s);
-                }
+        // cycles: FP32 sweeps to the cycle target, then the FP64 refinement;
+        // the stop test is the one on the refined (exact) |F|_1
+        DI_CUDA(cudaMemcpyAsync(hc, st->ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, s));
+        DI_CUDA(cudaStreamSynchronize(s));
+        for (int cycle = 0; hc->done == 0; cycle++) {
+            if (cycle == MAX_CYCLES) {
+                hc->done = 2;
+                break;
             }
-            DI_CUDA(cudaGetLastError());
+            DI_TRY(run_sweeps(g, st, SW_F32, o, s, pp));
+            DI_TRY(refine_pass(g, st, s));
+            refinements++;
             DI_CUDA(cudaMemcpyAsync(hc, st->ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, s));
+            DI_CUDA(cudaMemcpyAsync(st->host_rctl, st->rctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, s));
             DI_CUDA(cudaStreamSynchronize(s));
-            if (hc->done) break;
+            refine_links += (int64_t)st->host_rctl->sweep_links;
         }
     }
     DI_CUDA(cudaEventRecord(st->ev1, s));
+    const unsigned done = hc->done;   // (graph mode: read below)
     k_reduce<<<(unsigned)st->ntiles, SEL_THREADS, 0, s>>>(st->F, st->H, static_cast<const Off *>(g->rp),
                                                           n, st->ntiles, st->tile_l1, st->tile_l,
-                                                          st->ctl, RED_FINAL);
+                                                          st->ctl, RED_FINAL, nullptr);
     count_launches(1);
     DI_CUDA(cudaGetLastError());
     DI_CUDA(cudaMemcpyAsync(hc, st->ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, s));
     DI_CUDA(cudaStreamSynchronize(s));
+    if (f32) hc->done = done;   // a cycle cap decided on the host
     float ms = 0.f;
     DI_CUDA(cudaEventElapsedTime(&ms, st->ev0, st->ev1));
-    if (graph_mode) count_launches(3 * ((int64_t)hc->sweep + 1));
-    if (npairs) {
+    if (o->use_graph && !o->profile) count_launches(3 * ((int64_t)hc->sweep + refinements + 1));
+    if (pp.npairs) {
         // push launch i follows selection i; selections past the converged
         // sweep returned at once and their pushes found no work
         static unsigned long long hstats[2 * STAT_CAP];
-        const int ran = (int)((int64_t)hc->sweep < npairs ? (int64_t)hc->sweep : npairs);
+        const int ran = (int)((int64_t)hc->sweep < pp.npairs ? (int64_t)hc->sweep : pp.npairs);
         DI_CUDA(cudaMemcpy(hstats, st->stats, sizeof(unsigned long long) * 2 * ran, cudaMemcpyDeviceToHost));
         for (int i = 0; i < ran; i++) {
             if (hstats[2 * i] == 0) continue;
@@ -1080,6 +1378,8 @@ di_status solve_loop(di_graph_s *g, di_state_s *st, double tol, const di_opts *o
         info->push_launches = push_launches;
         info->push_edges = push_edges;
         info->push_entries = push_entries;
+        info->refinements = refinements;
+        info->refine_links = refine_links;
     }
     if (hc->err) return DI_ERR_DEVICE_TIMEOUT;
     if (hc->done == 2) return DI_ERR_NOT_CONVERGED;
@@ -1139,7 +1439,7 @@ di_status state_l(di_graph_s *g, di_state_s *st, double *l, cudaStream_t s)
     DI_CUDA(cudaMemsetAsync(ctl, 0, sizeof(DevCtl), s));
     k_reduce<<<(unsigned)st->ntiles, SEL_THREADS, 0, s>>>(st->F, st->H, static_cast<const Off *>(g->rp),
                                                           g->n, st->ntiles, st->tile_l1, st->tile_l, ctl,
-                                                          RED_FINAL);
+                                                          RED_FINAL, nullptr);
     count_launches(1);
     DI_CUDA(cudaGetLastError());
     DI_CUDA(cudaMemcpyAsync(l, &ctl->final_l, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -1186,7 +1486,7 @@ di_status select_only(di_graph_s *g, const double *F, double theta, int32_t *ids
             k_dscale<<<grid_for(n, 256), 256, 0, s>>>(static_cast<const Off *>(g->rp), g->wsum, n, 0.85,
                                                       st.dscale);
             count_launches(1);
-            launch_select(g, &st, s, 0, cudaGraphConditionalHandle{}, sel_ids);
+            launch_select(g, &st, sweep_of(&st, SW_F64), s, 0, cudaGraphConditionalHandle{}, sel_ids);
             rc = scan_exclusive<uint32_t>(st.tile_diff, base, st.ntiles, tot, s);
             if (rc == DI_OK) {
                 k_compact_ids<<<(unsigned)st.ntiles, 256, 0, s>>>(sel_ids, st.tile_diff, base, ids);
