@@ -43,8 +43,8 @@ BATCH_FRAC = 0.01
 METRIC = "edge-pushes/s"
 WORKLOAD = ("web-like graph: 4,000,000 pages, 40,000,000 links, hosts lognormal(mean 100), "
             "80% intra-host links, Pareto(1.1) attractiveness, 15% dangling, Zipf(2.1) out-degree "
-            "in [1,50000]; d=0.85, uniform Z, plain FP64 solve to |F|_1/(1-d) <= 1e-9, then a 1% "
-            "link-update round trip (inject + re-converge, twice)")
+            "in [1,50000]; d=0.85, uniform Z, solve to |F|_1/(1-d) <= 1e-9 (fluid arithmetic: config "
+            "'precision'), then a 1% link-update round trip (inject + re-converge, twice)")
 GEN_KW = dict(n=4_000_000, m_target=40_000_000)
 
 
@@ -134,8 +134,9 @@ def run_reference(args, g):
             "e2e": {"value": val, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
-def config_dict(g, gi):
+def config_dict(g, gi, precision="f64"):
     c = {"workload": WORKLOAD, "n": g.n, "links": gi["nnz"] if gi else None, "d": D, "tol": TOL,
+         "precision": precision,
          "z": "uniform", "batch_frac": BATCH_FRAC, "parallelism": "replicas (one independent solve per GPU)",
          "l2": "inputs larger than L2 (160 MB of link targets); L2 flushed (256 MB write) between steps"}
     if gi:
@@ -155,15 +156,46 @@ def cpu_baseline(g, cp, ci):
             "time_to_tol_s": dt, "edge_pushes": info["edge_pushes"], "diffusions": info["diffusions"]}
 
 
-def traffic_for(kernel_src: str):
+def oracle_x(g, cp, ci):
+    """The oracle's x to 1e-12 (|F|_1/(1-d)), to state each form's error."""
+    import oracle
+    H, _, _, _ = oracle.di_solve(g.n, cp, ci, None, D, None, tol=1e-12)
+    return H
+
+
+def traffic_for(kernel_src: str, precision: str):
     """DRAM traffic per push launch from the committed ncu summary, if it was
     taken on the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", "push_web4m_traffic.json")
+    path = os.path.join(ROOT, "profiles", f"push_web4m_{precision}_traffic.json")
     if not os.path.exists(path):
         return None
     rec = json.load(open(path))
     h = hashlib.sha1(open(kernel_src, "rb").read()).hexdigest()
     return rec.get("dram_bytes_per_launch") if rec.get("source_sha1") == h else None
+
+
+def forms(st, G, g, torch, x_ref, reps=5):
+    """Time to tol of a from-scratch solve in each form (L2 flushed before each
+    run, CUDA events inside the library), with the L1 error of the returned H
+    against the FP64 oracle's x when it is available."""
+    from paper_1501_06350_gb300 import _lib
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    out = {}
+    for name, kw in (("f64", {}), ("f32_refined", {"precision": _lib.DI_PREC_F32})):
+        ts, info, H = [], None, None
+        for _ in range(reps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            H, info = st.solve(D, tol=TOL, **kw)
+            ts.append(info["time_ms"])
+        rec = {"time_to_tol_ms": statistics.median(ts), "min_ms": min(ts), "sweeps": info["sweeps"],
+               "edge_pushes": info["edge_pushes"], "refinements": info["refinements"],
+               "refine_links": info["refine_links"], "resid_l1": info["resid_l1"], "bound": info["bound"]}
+        if x_ref is not None:
+            rec["err_l1_vs_oracle"] = float(np.abs(H.cpu().numpy() - x_ref).sum())
+        out[name] = rec
+    out["f32_speedup"] = out["f64"]["time_to_tol_ms"] / out["f32_refined"]["time_to_tol_ms"]
+    return out
 
 
 # ------------------------------------------------------------------ main
@@ -180,6 +212,11 @@ def main():
                     help="frontier threshold factor c (default: the library default)")
     ap.add_argument("--eager", action="store_true",
                     help="launch the sweep kernels one by one instead of the CUDA-graph loop")
+    ap.add_argument("--precision", choices=["f64", "f32"], default="f64",
+                    help="fluid arithmetic of the timed step: plain FP64, or FP32 fluid with FP64 "
+                         "history and FP64 residual refinement")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the side-by-side time to tol of both forms")
     args = ap.parse_args()
     if args.warmup < 3 and not args.small:
         ap.error("--warmup must be >= 3")
@@ -215,6 +252,8 @@ def main():
 
     ug = 0 if args.eager else 1
     sopt = {} if args.theta is None else {"theta_factor": args.theta}
+    if args.precision == "f32":
+        sopt["precision"] = _lib.DI_PREC_F32
 
     def step():
         H, i1 = st.solve(D, tol=TOL, use_graph=ug, **sopt)
@@ -273,17 +312,20 @@ def main():
     _, prof = st.solve(D, tol=TOL, profile=1, **sopt)
     per_launch_links = prof["push_edges"] / max(prof["push_launches"], 1)
     push_avg_s = prof["push_ms"] / 1e3 / max(prof["push_launches"], 1)
-    alg_bytes = 12.0 * per_launch_links
+    link_bytes = 8.0 if args.precision == "f32" else 12.0   # 4 B target + the fluid word added
+    alg_bytes = link_bytes * per_launch_links
     peaks = {}
     pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(pk_path):
         peaks = json.load(open(pk_path))
     peak = peaks.get("hbm_gbs", 6800.0)
     achieved = alg_bytes / push_avg_s / 1e9
-    traffic = traffic_for(os.path.join(ROOT, "paper_1501_06350_gb300", "csrc", "di_solve.cu"))
+    traffic = traffic_for(os.path.join(ROOT, "paper_1501_06350_gb300", "csrc", "di_solve.cu"), args.precision)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
-                "kernel": "k_push", "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+                "kernel": "k_push<float>" if args.precision == "f32" else "k_push<double>",
+                "bytes_per_link": link_bytes,
+                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
                 "algorithmic_bytes_per_launch": alg_bytes, "links_per_launch": per_launch_links,
                 "launches": prof["push_launches"], "push_ms_avg": 1e3 * push_avg_s,
                 "push_share_of_solve": prof["push_ms"] / prof["time_ms"] if prof["time_ms"] else None}
@@ -291,8 +333,9 @@ def main():
     solve_pushes = statistics.median([i1["edge_pushes"] for i1, _, _ in infos])
     out = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": config_dict(g, gi),
+           "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32 fluid / f64 history" if args.precision == "f32" else "f64", "data": "synthetic",
+           "config": config_dict(g, gi, args.precision),
            "time_to_tol_ms": statistics.median(solve_ms),
            "solve": {"edge_pushes": solve_pushes, "sweeps": statistics.median([i1["sweeps"] for i1, _, _ in infos]),
                      "edge_pushes_per_s": solve_pushes / (statistics.median(solve_ms) / 1e3),
@@ -304,8 +347,12 @@ def main():
 
     if rank == 0 and world == 1 and not args.no_e2e:
         out["e2e"] = e2e(args, g, src, dst, op, di, torch)
+    x_ref = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(g, cp, ci)
+        x_ref = oracle_x(g, cp, ci)
+    if rank == 0 and not args.no_forms:
+        out["forms"] = forms(st, G, g, torch, x_ref)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:

@@ -191,7 +191,7 @@ struct di_state_s {
 
 namespace di {
 constexpr int SEL_THREADS = 512;
-constexpr int SEL_PER_THREAD = 4;
+constexpr int SEL_PER_THREAD = 16;
 constexpr int TILE = SEL_THREADS * SEL_PER_THREAD;   // nodes per selection tile
 constexpr int PUSH_THREADS = 256;
 constexpr int HUB_DEG = 256;                         // longer rows are pushed as pieces

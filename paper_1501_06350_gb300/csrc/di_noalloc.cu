@@ -11,8 +11,10 @@ namespace {
 
 using namespace di;
 
-// Largest graph served: NOALLOC_MAX_TILES selection tiles of TILE nodes.
-constexpr int64_t NOALLOC_MAX_TILES = int64_t(1) << 16;
+// Largest graph served: 2^16 * 2048 = 134,217,728 nodes, i.e. this many
+// reduction tiles of TILE nodes.
+constexpr int64_t NOALLOC_MAX_NODES = (int64_t(1) << 16) * 2048;
+constexpr int64_t NOALLOC_MAX_TILES = (NOALLOC_MAX_NODES + TILE - 1) / TILE;
 constexpr size_t CTL_BYTES = (sizeof(DevCtl) + 255) / 256 * 256;
 constexpr size_t SCRATCH_BYTES = CTL_BYTES + 2 * NOALLOC_MAX_TILES * sizeof(double);
 
@@ -44,8 +46,7 @@ di_status scratch_on(int device, unsigned char **out)
 extern "C" di_status di_residual_l1_noalloc(di_graph_t g, const double *v, double *out, void *stream)
 {
     if (!g || !v || !out) return DI_ERR_INVALID_ARG;
-    const int64_t ntiles = (g->n + TILE - 1) / TILE;
-    if (ntiles > NOALLOC_MAX_TILES) return DI_ERR_INVALID_ARG;
+    if (g->n > NOALLOC_MAX_NODES) return DI_ERR_INVALID_ARG;
     int prev = -1;
     if (cudaGetDevice(&prev) != cudaSuccess) return DI_ERR_CUDA;
     if (prev != g->device && cudaSetDevice(g->device) != cudaSuccess) return DI_ERR_CUDA;

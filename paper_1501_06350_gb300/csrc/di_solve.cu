@@ -280,8 +280,11 @@ __global__ void __launch_bounds__(SEL_THREADS) k_reduce(const double *v, const d
     double f[P];
     loadP<P>(v, i0, n, f);
     if (v32) {
-        static_assert(P == 4, "one 16-byte store per thread");
-        *reinterpret_cast<float4 *>(v32 + i0) = make_float4((float)f[0], (float)f[1], (float)f[2], (float)f[3]);
+        static_assert(P % 4 == 0, "whole 16-byte stores");
+#pragma unroll
+        for (int q = 0; q < P / 4; q++)
+            *reinterpret_cast<float4 *>(v32 + i0 + 4 * q) =
+                make_float4((float)f[4 * q], (float)f[4 * q + 1], (float)f[4 * q + 2], (float)f[4 * q + 3]);
     }
     double a = fabs(f[0]);
 #pragma unroll
@@ -375,22 +378,27 @@ __device__ __forceinline__ void st_word(float *a, unsigned v, unsigned long long
     asm volatile("st.global.L2::cache_hint.b32 [%0], %1, %2;" ::"l"(a), "r"(v), "l"(pol) : "memory");
 }
 
-// The 4 consecutive fluid words of a selection thread (0 past the end).
-__device__ __forceinline__ void load4_keep(const double *F, int64_t i0, int64_t n, unsigned long long *fb,
+// The P consecutive fluid words of a selection thread (0 past the end).
+template <int P>
+__device__ __forceinline__ void loadw_keep(const double *F, int64_t i0, int64_t n, unsigned long long *fb,
                                            unsigned long long pol)
 {
-    loadP_keep<4>(F, i0, n, fb, pol);
+    loadP_keep<P>(F, i0, n, fb, pol);
 }
-__device__ __forceinline__ void load4_keep(const float *F, int64_t i0, int64_t n, unsigned *fb,
+template <int P>
+__device__ __forceinline__ void loadw_keep(const float *F, int64_t i0, int64_t n, unsigned *fb,
                                            unsigned long long pol)
 {
-    if (i0 + 3 < n) {
-        asm volatile("ld.global.L2::cache_hint.v4.b32 {%0, %1, %2, %3}, [%4], %5;"
-                     : "=r"(fb[0]), "=r"(fb[1]), "=r"(fb[2]), "=r"(fb[3])
-                     : "l"(F + i0), "l"(pol));
+    static_assert(P % 4 == 0, "whole 16-byte words");
+    if (i0 + P - 1 < n) {
+#pragma unroll
+        for (int q = 0; q < P / 4; q++)
+            asm volatile("ld.global.L2::cache_hint.v4.b32 {%0, %1, %2, %3}, [%4], %5;"
+                         : "=r"(fb[4 * q]), "=r"(fb[4 * q + 1]), "=r"(fb[4 * q + 2]), "=r"(fb[4 * q + 3])
+                         : "l"(F + i0 + 4 * q), "l"(pol));
     } else {
 #pragma unroll
-        for (int k = 0; k < 4; k++) fb[k] = (i0 + k < n) ? ld_b32(F + i0 + k, pol) : 0u;
+        for (int k = 0; k < P; k++) fb[k] = (i0 + k < n) ? ld_b32(F + i0 + k, pol) : 0u;
     }
 }
 
@@ -422,8 +430,8 @@ __global__ void __launch_bounds__(SEL_THREADS)
     typedef typename FluidWord<T>::U U;
     constexpr int P = SEL_PER_THREAD;
     constexpr int NW = SEL_THREADS / 32;
-    static_assert(P == 4, "selection threads read 4 consecutive fluid words");
     static_assert(32 % P == 0, "a mask word must cover whole threads");
+    static_assert(TILE <= 65535, "per-tile counts are packed in 16 bits");
     __shared__ float s_fx[NW];
     __shared__ unsigned s_mx[NW], s_cnt[NW];
     __shared__ unsigned long long smu[NW + 1];
@@ -445,7 +453,7 @@ __global__ void __launch_bounds__(SEL_THREADS)
     const unsigned long long keep = pol_last();
 
     U fb[P];
-    load4_keep(F, i0, n, fb, keep);
+    loadw_keep<P>(F, i0, n, fb, keep);
     const unsigned hubw = (__ldg(hubbits + i0 / 32) >> (i0 % 32)) & ((1u << P) - 1u);
     float fx = 0.0f;
     unsigned selm = 0;
