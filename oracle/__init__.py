@@ -66,6 +66,10 @@ def _load():
         _lib.or_apply_batch.argtypes = [i64, P, P, P, i64, P, P, P, P, P, P, P]
         _lib.or_update_inject.restype = i64
         _lib.or_update_inject.argtypes = [i64, P, P, P, P, P, P, ctypes.c_double, P, P]
+        _lib.or_adjoint_jacobi.restype = i64
+        _lib.or_adjoint_jacobi.argtypes = [i64, P, P, P, ctypes.c_double, P, ctypes.c_double, i64, P]
+        _lib.or_grad_w.restype = None
+        _lib.or_grad_w.argtypes = [i64, P, P, P, ctypes.c_double, P, P, P]
     return _lib
 
 
@@ -190,6 +194,30 @@ def update_inject(n, old, new, d, H, F):
                               _p(np.ascontiguousarray(i1, dtype=np.int32)), _p(_f64(w1)), d,
                               _p(H), _p(F2))
     return F2, int(ch)
+
+
+def adjoint(n, ptr, idx, w, d, g, tol=1e-15, max_iters=100_000):
+    """lambda with (I - d P)^T lambda = g (Jacobi sweeps of the Neumann series,
+    stopped on the bound |lambda - lambda_k|_inf <= tol).  Returns (lambda, sweeps)."""
+    lib = _load()
+    lam = np.zeros(n)
+    it = lib.or_adjoint_jacobi(n, _p(np.ascontiguousarray(ptr, dtype=np.int64)),
+                               _p(np.ascontiguousarray(idx, dtype=np.int32)), _p(_f64(w)), d,
+                               _p(_f64(g)), tol, max_iters, _p(lam))
+    if it < 0:
+        raise ValueError("invalid adjoint input")
+    return lam, int(it)
+
+
+def grad_w(n, ptr, idx, w, d, x, lam):
+    """dL/dw per link of the canonical out-CSR for L = g . x, given x and the
+    adjoint lambda: d x_j / W_j (lambda_k - (P^T lambda)_j)."""
+    lib = _load()
+    ptr = np.ascontiguousarray(ptr, dtype=np.int64)
+    out = np.zeros(max(int(ptr[-1]), 1))
+    lib.or_grad_w(n, _p(ptr), _p(np.ascontiguousarray(idx, dtype=np.int32)), _p(_f64(w)), d,
+                  _p(_f64(x)), _p(_f64(lam)), _p(out))
+    return out[:int(ptr[-1])]
 
 
 # --------------------------------------------------------------------------

@@ -23,6 +23,10 @@
  *   or_apply_batch       pinned (brute-force set semantics on tiny inputs)
  *   or_update_inject     pinned (Theorem update: resumed DI reaches the dense
  *                        solution of the new matrix)
+ *   or_adjoint_jacobi    pinned (dense solve of (I - dP)^T lambda = g, the
+ *                        duality g . x = (1 - d) lambda . Z, closed forms)
+ *   or_grad_w            pinned (central finite differences of g . x(w) with
+ *                        x from the dense solve)
  */
 #include <math.h>
 #include <stdint.h>
@@ -366,4 +370,61 @@ int64_t or_update_inject(int64_t n, const int64_t *ptr, const int32_t *idx, cons
     free(W);
     free(NW);
     return changed;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Adjoint of the PageRank solve (not in the paper; the backward pass of      */
+/* x = (1 - d)(I - d P)^-1 Z for a loss L = g . x).  lambda solves             */
+/* (I - d P)^T lambda = g, i.e. lambda = g + d P^T lambda, whose Neumann       */
+/* series sum_k d^k (P^T)^k g converges because every row of P^T sums to at    */
+/* most 1 (the columns of P do, Section 2.1): |P^T v|_inf <= |v|_inf.          */
+/* Plain Jacobi sweeps lambda_{k+1} = g + d P^T lambda_k from lambda_0 = g,    */
+/* with (P^T lambda)_j = sum over links j -> i of P[i][j] lambda_i formed row  */
+/* by row of the out-CSR.  |lambda - lambda_k|_inf <= d/(1-d) |lambda_k -      */
+/* lambda_{k-1}|_inf, so the loop stops once that bound is at most tol.        */
+/* Returns the number of sweeps, or OR_BAD_INPUT.                              */
+/* ------------------------------------------------------------------------- */
+int64_t or_adjoint_jacobi(int64_t n, const int64_t *ptr, const int32_t *idx, const double *w, double d,
+                          const double *g, double tol, int64_t max_iters, double *lambda)
+{
+    if (n < 1 || !(d > 0.0 && d < 1.0) || !(tol > 0.0)) return OR_BAD_INPUT;
+    double *W = row_scale(n, ptr, w);
+    double *next = malloc(sizeof(double) * (size_t)n);
+    for (int64_t i = 0; i < n; i++) lambda[i] = g[i];
+    int64_t it = 0;
+    while (it < max_iters) {
+        double change = 0.0;
+        for (int64_t j = 0; j < n; j++) {
+            double s = 0.0;
+            for (int64_t e = ptr[j]; e < ptr[j + 1]; e++) s += p_entry(W, w, j, e) * lambda[idx[e]];
+            next[j] = g[j] + d * s;
+            double c = fabs(next[j] - lambda[j]);
+            if (c > change) change = c;
+        }
+        memcpy(lambda, next, sizeof(double) * (size_t)n);
+        it++;
+        if (d / (1.0 - d) * change <= tol) break;
+    }
+    free(next);
+    free(W);
+    return it;
+}
+
+/* Gradient of L = g . x with respect to the link weights (not in the paper). */
+/* With P[i][j] = w(j,i) / W_j (Section 2.1, Eq. def-p), W_j = sum_k w(j,k):  */
+/*   dL/dP[a][b] = d lambda_a x_b, and dP[i][j]/dw(j,k) = [i = k]/W_j -       */
+/*   w(j,i)/W_j^2, so dL/dw(j,k) = d x_j / W_j (lambda_k - (P^T lambda)_j).   */
+/* grad has one entry per link of the canonical out-CSR, in its order; an     */
+/* unweighted graph is treated as all weights 1.  dL/dZ = (1 - d) lambda.      */
+void or_grad_w(int64_t n, const int64_t *ptr, const int32_t *idx, const double *w, double d,
+               const double *x, const double *lambda, double *grad)
+{
+    double *W = row_scale(n, ptr, w);
+    for (int64_t j = 0; j < n; j++) {
+        if (ptr[j + 1] == ptr[j]) continue;
+        double s = 0.0;
+        for (int64_t e = ptr[j]; e < ptr[j + 1]; e++) s += p_entry(W, w, j, e) * lambda[idx[e]];
+        for (int64_t e = ptr[j]; e < ptr[j + 1]; e++) grad[e] = d * x[j] / W[j] * (lambda[idx[e]] - s);
+    }
+    free(W);
 }
