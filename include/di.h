@@ -98,6 +98,7 @@ typedef struct {
     int64_t push_entries;    /* profile: frontier entries read by those launches            */
     int64_t refinements;     /* DI_PREC_F32: FP64 refinement passes run by this call         */
     int64_t refine_links;    /* DI_PREC_F32: links pushed by those passes                    */
+    double resid_inf;        /* max_i |F_i| of the returned state (FP64)                     */
 } di_info;
 
 /* Fill *o with the defaults: theta_factor 1, max_sweeps 100000, check_every 8,
@@ -199,6 +200,39 @@ di_status di_state_export(di_state_t s, double *H, double *F, double *l, int mem
  * damping d for later di_resume calls.  Both float64[n], finite. */
 di_status di_state_import(di_state_t s, const double *H, const double *F, double d, int mem,
                           void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Adjoint (backward pass of the solve; the paper has no counterpart).
+ *
+ * For a loss L = g . x with x = (1 - d)(I - d P)^-1 Z (Section 2.1,
+ * Eq. pagerank-pf), the adjoint lambda solves (I - d P)^T lambda = g.  It is
+ * computed by the fluid diffusion of Section 3.1 on the reverse graph (node i
+ * sends d F_i P[i][j] to every j with a link j -> i), with the same sweep
+ * kernels as di_solve: fluid F_0 = g, history H_0 = 0.  Rows of P^T sum to at
+ * most 1, so the stop test is on the infinity norm:
+ * |lambda - H|_inf <= |F|_inf / (1 - d) <= tol, and the frontier threshold is
+ * capped at (1 - d)/2 max |F_i| (max |F| then shrinks every sweep).
+ *   d        damping, 0 < d < 1
+ *   gvec     float64[n] in `mem`: dL/dx, finite
+ *   x        float64[n] in `mem`: the forward solution (e.g. H_out of di_solve);
+ *            required when grad_w_out is given, else may be NULL
+ *   tol      > 0, bound on |lambda - lambda_out|_inf
+ *   opts     NULL = defaults; precision must be DI_PREC_F64; theta_factor,
+ *            max_sweeps, use_graph, check_every, profile as for di_solve
+ *   lambda_out  float64[n] or NULL: lambda
+ *   grad_Z_out  float64[n] or NULL: dL/dZ = (1 - d) lambda
+ *   grad_w_out  float64[nnz] or NULL: dL/dw per link of the canonical out-CSR
+ *            (the order of di_graph_export_csr): for a link j -> k with
+ *            P[k][j] = w(j,k) / W_j (unweighted graphs: all w = 1),
+ *            dL/dw(j,k) = d x_j / W_j (lambda_k - (P^T lambda)_j)
+ *   info     may be NULL; bound = |F|_inf / (1 - d), resid_inf = |F|_inf
+ * The reverse graph and its solver state are built on the first call for the
+ * graph's current link set and kept with the graph (about the size of the
+ * graph plus one solver state).  DI_ERR_NOT_CONVERGED: sweep cap reached; the
+ * outputs hold the reached state. */
+di_status di_adjoint(di_graph_t g, double d, const double *gvec, const double *x, double tol,
+                     const di_opts *opts, double *lambda_out, double *grad_Z_out, double *grad_w_out,
+                     di_info *info, int mem, void *stream);
 
 /* ---------------------------------------------------------------------------
  * Single steps of the sweep, exposed for verification.

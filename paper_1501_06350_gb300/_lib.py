@@ -45,7 +45,8 @@ class di_info(ctypes.Structure):
                 ("edge_pushes", ctypes.c_int64), ("time_ms", ctypes.c_double),
                 ("push_ms", ctypes.c_double), ("push_launches", ctypes.c_int64),
                 ("push_edges", ctypes.c_int64), ("push_entries", ctypes.c_int64),
-                ("refinements", ctypes.c_int64), ("refine_links", ctypes.c_int64)]
+                ("refinements", ctypes.c_int64), ("refine_links", ctypes.c_int64),
+                ("resid_inf", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -87,6 +88,8 @@ SIGNATURES = {
     "di_update_edges": (INT, [P, P, I64, P, P, P, P, INT, P]),
     "di_state_export": (INT, [P, P, P, P, INT, P]),
     "di_state_import": (INT, [P, P, P, ctypes.c_double, INT, P]),
+    "di_adjoint": (INT, [P, ctypes.c_double, P, P, ctypes.c_double, ctypes.POINTER(di_opts), P, P, P,
+                         ctypes.POINTER(di_info), INT, P]),
     "di_frontier_select": (INT, [P, P, ctypes.c_double, P, ctypes.POINTER(I64), INT, P]),
     "di_residual_l1": (INT, [P, P, P, INT, P]),
     "di_residual_l1_noalloc": (INT, [P, P, P, P]),

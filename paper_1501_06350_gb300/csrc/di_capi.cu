@@ -333,6 +333,52 @@ di_status di_state_import(di_state_t st, const double *H, const double *F, doubl
     return DI_OK;
 }
 
+di_status di_adjoint(di_graph_t g, double d, const double *gvec, const double *x, double tol, const di_opts *opts,
+                     double *lambda_out, double *grad_Z_out, double *grad_w_out, di_info *info, int mem,
+                     void *stream)
+{
+    if (!g || !gvec || !mem_ok(mem)) return DI_ERR_INVALID_ARG;
+    if (!(d > 0.0 && d < 1.0) || !(tol > 0.0) || !isfinite(tol)) return DI_ERR_INVALID_ARG;
+    if (grad_w_out && !x) return DI_ERR_INVALID_ARG;
+    di_opts o;
+    di_opts_default(&o);
+    if (opts) o = *opts;
+    DI_TRY(opts_ok(&o));
+    if (o.precision != DI_PREC_F64) return DI_ERR_INVALID_ARG;
+    DeviceScope ds(g->device);
+    cudaStream_t s = as_stream(stream);
+    const int64_t n = g->n;
+    Temps t(s);
+    const double *gd = nullptr, *xd = nullptr;
+    DI_TRY(stage_in(gvec, n, mem, t, &gd, s));
+    DI_TRY(stage_in(x, n, mem, t, &xd, s));
+    bool ok = false;
+    DI_TRY(check_finite(gd, n, &ok, s));
+    if (!ok) return DI_ERR_INVALID_ARG;
+    if (xd) {
+        DI_TRY(check_finite(xd, n, &ok, s));
+        if (!ok) return DI_ERR_INVALID_ARG;
+    }
+    double *lam = lambda_out, *gz = grad_Z_out, *gw = grad_w_out;
+    const int64_t m = g->nnz;
+    if (mem == DI_MEM_HOST) {
+        if (lam) DI_TRY(t.get(&lam, n));
+        if (gz) DI_TRY(t.get(&gz, n));
+        if (gw) DI_TRY(t.get(&gw, m > 0 ? m : 1));
+    }
+    di_info inf = {};
+    di_status rc = adjoint(g, d, gd, xd, tol, &o, lam, gz, gw, &inf, s);
+    if (rc != DI_OK && rc != DI_ERR_NOT_CONVERGED) return rc;
+    if (mem == DI_MEM_HOST) {
+        if (lam) DI_CUDA(cudaMemcpyAsync(lambda_out, lam, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+        if (gz) DI_CUDA(cudaMemcpyAsync(grad_Z_out, gz, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+        if (gw && m) DI_CUDA(cudaMemcpyAsync(grad_w_out, gw, sizeof(double) * m, cudaMemcpyDeviceToHost, s));
+        DI_CUDA(cudaStreamSynchronize(s));
+    }
+    if (info) *info = inf;
+    return rc;
+}
+
 di_status di_frontier_select(di_graph_t g, const double *F, double theta, int32_t *ids, int64_t *count,
                              int mem, void *stream)
 {

@@ -475,6 +475,7 @@ di_status graph_create(int64_t n, int64_t nnz, const int64_t *ptr, const int32_t
 
 void graph_release(di_graph_s *g)
 {
+    reverse_release(g);
     cudaStream_t s = 0;
     dfree(g->rp, s);
     dfree(g->col, s);

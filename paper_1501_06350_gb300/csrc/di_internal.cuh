@@ -106,6 +106,11 @@ struct di_graph_s {
     int32_t *hot_node = nullptr;  // [HOT_K] page of each hot slot
     int nhot = 0;
     int64_t pcol_version = -1;
+    // reverse graph (links i -> j for every j -> i, weight P[i][j]) and the
+    // solver state of the adjoint, built on demand per version
+    struct di_graph_s *rev = nullptr;
+    struct di_state_s *rev_state = nullptr;
+    int64_t rev_version = -1;
     // in-link structure, built on demand
     int64_t *cp = nullptr;    // [n+1]
     int32_t *crow = nullptr;  // [nnz]
@@ -123,6 +128,9 @@ struct DevCtl {
     double final_l;        // sum of H over dangling nodes (final reduction)
     double sweep_stop;     // the sweep loop ends when its |F|_1 bound is at most this
     double refine_ratio;   // FP32 fluid: each cycle ends at refine_ratio x its starting |F|_1
+    double inf_cap;        // inf_norm: the threshold never exceeds inf_cap x max |F_i|
+    double final_max;      // max |F_i| of the final state (FP64)
+    double hot_scale;      // bound on what one sweep adds into one page: sets the push's fixed point
     unsigned long long diffusions;
     unsigned long long edge_pushes;
     unsigned long long sweep;         // pushes performed by this call
@@ -131,7 +139,7 @@ struct DevCtl {
     unsigned long long npieces;       // hub pieces cut by the plan (read by the push)
     unsigned long long sweep_links;   // links pushed by the running push
     unsigned long long nent;          // frontier nodes of the last selection (mask bits)
-    int pad_i;
+    int inf_norm;              // 1: stop test and threshold cap on max |F_i| (adjoint)
     unsigned int done;         // 0 running, 1 converged, 2 sweep cap
     unsigned int ticket2;      // last-block ticket of the reductions
     unsigned int err;          // reserved for device-side error flags
@@ -174,6 +182,8 @@ struct di_state_s {
     unsigned int *tile_diff = nullptr;
     float *tile_l1f = nullptr;               // |F|_1 partial, FP32 rounded upward
     unsigned *tile_maxf = nullptr;           // max |F_i|, FP32 bits rounded downward
+    unsigned *tile_maxu = nullptr;           // max |F_i|, FP32 bits rounded upward
+    double *tile_max = nullptr;              // FP64 max partials of the reductions
     double *tile_l1 = nullptr;               // FP64 partials of the reductions
     double *tile_l = nullptr;
     DevCtl *ctl = nullptr;
@@ -217,7 +227,11 @@ di_status state_alloc(di_state_s *st, cudaStream_t s);
 di_status state_prepare_graph(di_graph_s *g, di_state_s *st, cudaStream_t s);
 di_status state_free(di_state_s *st);
 di_status solve_loop(di_graph_s *g, di_state_s *st, double tol, const di_opts *o, di_info *info,
-                     cudaStream_t s, bool fresh, const double *Z_dev);
+                     cudaStream_t s, bool fresh, const double *Z_dev, bool inf_norm = false);
+di_status graph_build_reverse(di_graph_s *g, cudaStream_t s);
+void reverse_release(di_graph_s *g);
+di_status adjoint(di_graph_s *g, double d, const double *gvec, const double *x, double tol, const di_opts *o,
+                  double *lambda, double *grad_Z, double *grad_w, di_info *info, cudaStream_t s);
 di_status l1_device(di_graph_s *g, const double *v, double *out_host, cudaStream_t s);
 di_status l1_device_into(di_graph_s *g, const double *v, double *part_l1, double *part_l, DevCtl *ctl,
                          double *out_host, cudaStream_t s);

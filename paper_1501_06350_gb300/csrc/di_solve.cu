@@ -268,9 +268,31 @@ __device__ __forceinline__ void loadP(const double *F, int64_t i0, int64_t n, do
 // the tile, 0 past n) and sets the targets of the next cycle.
 enum { RED_PLAIN = 0, RED_INIT = 1, RED_FINAL = 2, RED_CYCLE = 3 };
 
+// Deterministic block max of non-negative doubles (returned to every thread).
+template <int NT>
+__device__ __forceinline__ double block_max(double v, double *sm)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(FULL, v, o));
+    if (lane == 0) sm[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        double x = lane < NT / 32 ? sm[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(FULL, x, o));
+        if (lane == 0) sm[NT / 32] = x;
+    }
+    __syncthreads();
+    double r = sm[NT / 32];
+    __syncthreads();
+    return r;
+}
+
 __global__ void __launch_bounds__(SEL_THREADS) k_reduce(const double *v, const double *H, const Off *rp,
                                                        int64_t n, int64_t ntiles, double *part_l1,
-                                                       double *part_l, DevCtl *ctl, int mode, float *v32)
+                                                       double *part_l, double *part_max, DevCtl *ctl, int mode,
+                                                       float *v32)
 {
     __shared__ double sm[SEL_THREADS / 32 + 1];
     __shared__ int s_last;
@@ -286,9 +308,12 @@ __global__ void __launch_bounds__(SEL_THREADS) k_reduce(const double *v, const d
             *reinterpret_cast<float4 *>(v32 + i0 + 4 * q) =
                 make_float4((float)f[4 * q], (float)f[4 * q + 1], (float)f[4 * q + 2], (float)f[4 * q + 3]);
     }
-    double a = fabs(f[0]);
+    double a = fabs(f[0]), mxv = fabs(f[0]);
 #pragma unroll
-    for (int k = 1; k < P; k++) a += fabs(f[k]);
+    for (int k = 1; k < P; k++) {
+        a += fabs(f[k]);
+        mxv = fmax(mxv, fabs(f[k]));
+    }
     double l = 0.0;
     if (H) {
 #pragma unroll
@@ -299,9 +324,11 @@ __global__ void __launch_bounds__(SEL_THREADS) k_reduce(const double *v, const d
     }
     a = block_sum_det<SEL_THREADS>(a, sm);
     l = block_sum_det<SEL_THREADS>(l, sm);
+    if (part_max) mxv = block_max<SEL_THREADS>(mxv, sm);
     if (threadIdx.x == 0) {
         part_l1[tile] = a;
         part_l[tile] = l;
+        if (part_max) part_max[tile] = mxv;
         __threadfence();
         const unsigned t = atomicAdd(&ctl->ticket2, 1u);
         s_last = (t == (unsigned)(ntiles - 1));
@@ -309,15 +336,18 @@ __global__ void __launch_bounds__(SEL_THREADS) k_reduce(const double *v, const d
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    double sa = 0.0, sl = 0.0;
+    double sa = 0.0, sl = 0.0, smx = 0.0;
     for (int64_t k = threadIdx.x; k < ntiles; k += SEL_THREADS) {
         sa += __ldcg(part_l1 + k);
         sl += __ldcg(part_l + k);
+        if (part_max) smx = fmax(smx, __ldcg(part_max + k));
     }
     sa = block_sum_det<SEL_THREADS>(sa, sm);
     sl = block_sum_det<SEL_THREADS>(sl, sm);
+    if (part_max) smx = block_max<SEL_THREADS>(smx, sm);
     if (threadIdx.x == 0) {
         ctl->ticket2 = 0;
+        ctl->final_max = smx;
         if (mode == RED_INIT || mode == RED_CYCLE) {
             // a loop that ended in its stop test leaves the hubs of its last
             // selection listed (nobody took them): start the next one clean
@@ -328,7 +358,7 @@ __global__ void __launch_bounds__(SEL_THREADS) k_reduce(const double *v, const d
             ctl->theta = ctl->theta_factor * sa / (double)n;
             if (mode == RED_INIT) {
                 ctl->sweep_stop = ctl->stop_l1;
-                ctl->done = sa <= ctl->stop_l1 ? 1u : 0u;
+                ctl->done = (ctl->inf_norm ? smx : sa) <= ctl->stop_l1 ? 1u : 0u;
             } else {
                 // FP32 cycle: run to refine_ratio x the exact |F|_1 (never
                 // further than half the final target); a reached sweep cap
@@ -424,7 +454,7 @@ template <typename T>
 __global__ void __launch_bounds__(SEL_THREADS)
     k_select(const T *F, int64_t n, unsigned *mask, const unsigned *__restrict__ hubbits,
              unsigned *hub_list, unsigned *tile_cnt, unsigned *tile_diff, float *tile_l1f, unsigned *tile_maxf,
-             DevCtl *ctl, int use_cond, cudaGraphConditionalHandle cond,
+             unsigned *tile_maxu, DevCtl *ctl, int use_cond, cudaGraphConditionalHandle cond,
              int32_t *sel_ids)
 {
     typedef typename FluidWord<T>::U U;
@@ -433,7 +463,7 @@ __global__ void __launch_bounds__(SEL_THREADS)
     static_assert(32 % P == 0, "a mask word must cover whole threads");
     static_assert(TILE <= 65535, "per-tile counts are packed in 16 bits");
     __shared__ float s_fx[NW];
-    __shared__ unsigned s_mx[NW], s_cnt[NW];
+    __shared__ unsigned s_mx[NW], s_mu[NW], s_cnt[NW];
     __shared__ unsigned long long smu[NW + 1];
     volatile DevCtl *vc = ctl;
     if (vc->done) {
@@ -457,14 +487,16 @@ __global__ void __launch_bounds__(SEL_THREADS)
     const unsigned hubw = (__ldg(hubbits + i0 / 32) >> (i0 % 32)) & ((1u << P) - 1u);
     float fx = 0.0f;
     unsigned selm = 0;
-    unsigned mb = 0;
+    unsigned mb = 0, mu = 0;
 #pragma unroll
     for (int k = 0; k < P; k++) {
         const U b = fb[k] & FluidWord<T>::ABS;
-        fx = __fadd_ru(fx, __uint_as_float(up32(b)));
+        const unsigned bu = up32(b);
+        fx = __fadd_ru(fx, __uint_as_float(bu));
         if ((i0 + k < n) && b != 0 && b >= tb) selm |= 1u << k;
         const unsigned md = down32(b);
         mb = md > mb ? md : mb;
+        mu = bu > mu ? bu : mu;
     }
     const unsigned bits = selm & ~hubw;   // taken by the push
     const unsigned hubs = selm & hubw;    // taken by the plan
@@ -510,25 +542,30 @@ __global__ void __launch_bounds__(SEL_THREADS)
         fx = __fadd_ru(fx, __shfl_xor_sync(FULL, fx, o));
         const unsigned y = __shfl_xor_sync(FULL, mb, o);
         mb = y > mb ? y : mb;
+        const unsigned yu = __shfl_xor_sync(FULL, mu, o);
+        mu = yu > mu ? yu : mu;
         cnt += __shfl_xor_sync(FULL, cnt, o);
     }
     if (lane == 0) {
         s_fx[warp] = fx;
         s_mx[warp] = mb;
+        s_mu[warp] = mu;
         s_cnt[warp] = cnt;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         float t = s_fx[0];
-        unsigned mx = s_mx[0], c = s_cnt[0];
+        unsigned mx = s_mx[0], mxu = s_mu[0], c = s_cnt[0];
 #pragma unroll
         for (int w = 1; w < NW; w++) {
             t = __fadd_ru(t, s_fx[w]);
             mx = s_mx[w] > mx ? s_mx[w] : mx;
+            mxu = s_mu[w] > mxu ? s_mu[w] : mxu;
             c += s_cnt[w];
         }
         tile_l1f[tile] = t;
         tile_maxf[tile] = mx;
+        tile_maxu[tile] = mxu;
         tile_cnt[tile] = c & 0xffffu;
         tile_diff[tile] = c >> 16;
     }
@@ -549,12 +586,12 @@ __global__ void __launch_bounds__(SEL_THREADS)
     k_plan(T *Ft, T *Fd, double *Hs, const Off *__restrict__ rp, const double *__restrict__ dscale, int64_t n,
            int64_t ntiles, const unsigned *__restrict__ hub_list, Off *pc_row, Off *pc_len, double *pc_val,
            const unsigned *tile_cnt, const unsigned *tile_diff, const float *tile_l1f,
-           const unsigned *tile_maxf, DevCtl *ctl, int use_cond, cudaGraphConditionalHandle cond,
-           unsigned long long *stats)
+           const unsigned *tile_maxf, const unsigned *tile_maxu, DevCtl *ctl, int use_cond,
+           cudaGraphConditionalHandle cond, unsigned long long *stats)
 {
     typedef typename FluidWord<T>::U U;
     constexpr int NW = SEL_THREADS / 32;
-    __shared__ unsigned long long s_red[3][NW];
+    __shared__ unsigned long long s_red[4][NW];
     __shared__ float s_l1[NW];
     __shared__ unsigned s_go;
     volatile DevCtl *vc = ctl;
@@ -563,13 +600,14 @@ __global__ void __launch_bounds__(SEL_THREADS)
     // fixed order: thread-strided tiles, xor butterfly, warps in order; every
     // partial rounded upward, so every CTA gets the same upper bound
     float sfx = 0.0f;
-    unsigned long long sd = 0, sc = 0, mx = 0;
+    unsigned long long sd = 0, sc = 0, mx = 0, mu = 0;
     for (int64_t k = threadIdx.x; k < ntiles; k += SEL_THREADS) {
         sfx = __fadd_ru(sfx, __ldg(tile_l1f + k));
         sd += __ldg(tile_diff + k);
         sc += __ldg(tile_cnt + k);
-        const unsigned long long m = __ldg(tile_maxf + k);
+        const unsigned long long m = __ldg(tile_maxf + k), mm = __ldg(tile_maxu + k);
         mx = m > mx ? m : mx;
+        mu = mm > mu ? mm : mu;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -578,28 +616,34 @@ __global__ void __launch_bounds__(SEL_THREADS)
         sc += __shfl_xor_sync(FULL, sc, o);
         const unsigned long long y = __shfl_xor_sync(FULL, mx, o);
         mx = y > mx ? y : mx;
+        const unsigned long long yu = __shfl_xor_sync(FULL, mu, o);
+        mu = yu > mu ? yu : mu;
     }
     if (lane == 0) {
         s_l1[warp] = sfx;
         s_red[0][warp] = sd;
         s_red[1][warp] = sc;
         s_red[2][warp] = mx;
+        s_red[3][warp] = mu;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         sfx = s_l1[0];
-        sd = sc = mx = 0;
+        sd = sc = mx = mu = 0;
         for (int w = 0; w < NW; w++) {
             if (w) sfx = __fadd_ru(sfx, s_l1[w]);
             sd += s_red[0][w];
             sc += s_red[1][w];
             mx = s_red[2][w] > mx ? s_red[2][w] : mx;
+            mu = s_red[3][w] > mu ? s_red[3][w] : mu;
         }
         const double sa = (double)sfx;
+        const bool inf_norm = vc->inf_norm != 0;
         const unsigned long long sweep = vc->sweep;
         unsigned done = 0;
-        // every |F_i| and every partial sum was rounded up: an upper bound of |F_t|_1
-        if (sa <= vc->sweep_stop) done = 1;
+        // every |F_i| and every partial sum was rounded up: an upper bound of
+        // |F_t|_1 (or of max |F_i| in the infinity-norm mode)
+        if ((inf_norm ? (double)__uint_as_float((unsigned)mu) : sa) <= vc->sweep_stop) done = 1;
         else if (sweep >= vc->max_sweeps) done = 2;
         s_go = done == 0;
         if (blockIdx.x == 0) {
@@ -609,6 +653,12 @@ __global__ void __launch_bounds__(SEL_THREADS)
             if (stats && sweep >= 1 && sweep <= (unsigned long long)STAT_CAP) stats[2 * (sweep - 1)] = links;
             vc->sweep_links = 0;
             vc->l1 = sa;
+            // what one sweep can add into one page: at most the whole pushed
+            // volume d |F|_1 / (1 - d) < 8 |F|_1 (d <= 7/8) in the plain solve;
+            // on the reverse graph a page j receives d f_i P[i][j] from its
+            // out-neighbours i and the column of P sums to 1, so at most about
+            // d max |F| per take: 8 max |F| leaves a wide margin
+            vc->hot_scale = inf_norm ? 8.0 * (double)__uint_as_float((unsigned)mu) : sa;
             if (!done) {
                 vc->diffusions = vc->diffusions + sd;
                 vc->nent = sc;
@@ -619,6 +669,9 @@ __global__ void __launch_bounds__(SEL_THREADS)
                 // that (this covers a rounded average above several equal fluids).
                 const double fmax = (double)__uint_as_float((unsigned)mx);
                 if (sd == 0 && fmax < th) th = fmax;
+                // infinity-norm mode: theta <= inf_cap max |F_i| with inf_cap + d < 1,
+                // so max |F| shrinks by at least inf_cap + d per sweep
+                if (inf_norm && vc->inf_cap * fmax < th) th = vc->inf_cap * fmax;
                 vc->theta = th;
             }
             vc->push_ready = done ? 0u : 1u;
@@ -783,14 +836,13 @@ __global__ void __launch_bounds__(PUSH_THREADS)
     __shared__ unsigned long long s_hot[HOT_K];   // FP64: fixed point, units of 2^-hot_shift; FP32: floats
     volatile DevCtl *vc = ctl;
     if (!vc->push_ready) return;
-    // Fluid taken twice in one sweep (pushed in, then taken again) is counted
-    // twice, so the values pushed in a sweep add up to at most
-    // d |F|_1 / (1 - d) < 8 |F|_1 < 2^(e+3) in magnitude for d <= 7/8, and
-    // for larger d the sum of any one CTA's share stays far below that:
-    // 2^(58 - e) keeps every slot below 2^61.  (The refinement pass takes
-    // each node once: its pushes add up to at most d |D|_1 < |D|_1.)
+    // hot_scale bounds what this sweep adds into one page (see k_plan; fluid
+    // taken twice in one sweep counts twice, and for d > 7/8 the share of any
+    // one CTA stays far below the bound): with 2^(e-1) <= hot_scale < 2^e,
+    // units of 2^(e - 58) keep every slot below 2^61.  (The refinement pass
+    // takes each node once: its pushes add up to at most d |D|_1 < |D|_1.)
     int e = 0;
-    frexp(vc->l1, &e);
+    frexp(vc->hot_scale, &e);
     const int hot_shift = 58 - e;
     for (int k = threadIdx.x; k < nhot; k += PUSH_THREADS) s_hot[k] = 0ull;
     __syncthreads();
@@ -1007,6 +1059,8 @@ di_status state_alloc(di_state_s *st, cudaStream_t s)
     DI_TRY(dalloc_t(&st->tile_diff, st->ntiles, s));
     DI_TRY(dalloc_t(&st->tile_l1f, st->ntiles, s));
     DI_TRY(dalloc_t(&st->tile_maxf, st->ntiles, s));
+    DI_TRY(dalloc_t(&st->tile_maxu, st->ntiles, s));
+    DI_TRY(dalloc_t(&st->tile_max, st->ntiles, s));
     DI_TRY(dalloc_t(&st->tile_l1, st->ntiles, s));
     DI_TRY(dalloc_t(&st->tile_l, st->ntiles, s));
     DI_TRY(dalloc_t(&st->ctl, 1, s));
@@ -1032,7 +1086,7 @@ di_status state_free(di_state_s *st)
     if (st->gstream) cudaStreamDestroy(st->gstream);
     void *bufs[] = {st->F, st->H, st->dscale, st->mask, st->hubbits, st->hub_list, st->pc_row, st->pc_len,
                     st->pc_val, st->tile_cnt, st->tile_diff, st->tile_l1f, st->tile_maxf, st->tile_l1,
-                    st->tile_l, st->ctl, st->stats, st->F32, st->D, st->rctl};
+                    st->tile_l, st->ctl, st->stats, st->F32, st->D, st->rctl, st->tile_maxu, st->tile_max};
     for (void *p : bufs) dfree(p, s);
     if (st->host_ctl) cudaFreeHost(st->host_ctl);
     if (st->host_rctl) cudaFreeHost(st->host_rctl);
@@ -1069,11 +1123,11 @@ static void launch_select(di_graph_s *g, di_state_s *st, const Sweep &w, cudaStr
     if (w.kind == SW_F32)
         k_select<float><<<(unsigned)st->ntiles, SEL_THREADS, 0, s>>>(
             static_cast<const float *>(w.Ft), g->n, st->mask, st->hubbits, st->hub_list, st->tile_cnt,
-            st->tile_diff, st->tile_l1f, st->tile_maxf, w.ctl, use_cond, h, sel_ids);
+            st->tile_diff, st->tile_l1f, st->tile_maxf, st->tile_maxu, w.ctl, use_cond, h, sel_ids);
     else
         k_select<double><<<(unsigned)st->ntiles, SEL_THREADS, 0, s>>>(
             static_cast<const double *>(w.Ft), g->n, st->mask, st->hubbits, st->hub_list, st->tile_cnt,
-            st->tile_diff, st->tile_l1f, st->tile_maxf, w.ctl, use_cond, h, sel_ids);
+            st->tile_diff, st->tile_l1f, st->tile_maxf, st->tile_maxu, w.ctl, use_cond, h, sel_ids);
     count_launches(1);
 }
 
@@ -1084,7 +1138,7 @@ static void launch_plan(di_graph_s *g, di_state_s *st, const Sweep &w, cudaStrea
     unsigned long long *stats = w.kind == SW_REFINE ? nullptr : st->stats;
 #define DI_PLAN_ARGS                                                                                      \
     w.Hs, rp, st->dscale, g->n, st->ntiles, st->hub_list, st->pc_row, st->pc_len, st->pc_val, st->tile_cnt, \
-        st->tile_diff, st->tile_l1f, st->tile_maxf, w.ctl, use_cond, h, stats
+        st->tile_diff, st->tile_l1f, st->tile_maxf, st->tile_maxu, w.ctl, use_cond, h, stats
     if (w.kind == SW_F32)
         k_plan<float, false><<<PLAN_CTAS, SEL_THREADS, 0, s>>>(static_cast<float *>(w.Ft),
                                                                static_cast<float *>(w.Fd), DI_PLAN_ARGS);
@@ -1178,7 +1232,7 @@ di_status l1_device(di_graph_s *g, const double *v, double *out_host, cudaStream
     DI_TRY(t.get(&ctl, 1));
     DI_CUDA(cudaMemsetAsync(ctl, 0, sizeof(DevCtl), s));
     k_reduce<<<(unsigned)ntiles, SEL_THREADS, 0, s>>>(v, nullptr, static_cast<const Off *>(g->rp), g->n,
-                                                      ntiles, p1, p2, ctl, RED_PLAIN, nullptr);
+                                                      ntiles, p1, p2, nullptr, ctl, RED_PLAIN, nullptr);
     count_launches(1);
     DI_CUDA(cudaGetLastError());
     DI_CUDA(cudaMemcpyAsync(out_host, &ctl->final_l1, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -1194,7 +1248,7 @@ di_status l1_device_into(di_graph_s *g, const double *v, double *part_l1, double
     const int64_t ntiles = (g->n + TILE - 1) / TILE;
     DI_CUDA(cudaMemsetAsync(ctl, 0, sizeof(DevCtl), s));
     k_reduce<<<(unsigned)ntiles, SEL_THREADS, 0, s>>>(v, nullptr, static_cast<const Off *>(g->rp), g->n,
-                                                      ntiles, part_l1, part_l, ctl, RED_PLAIN, nullptr);
+                                                      ntiles, part_l1, part_l, nullptr, ctl, RED_PLAIN, nullptr);
     count_launches(1);
     DI_CUDA(cudaGetLastError());
     DI_CUDA(cudaMemcpyAsync(out_host, &ctl->final_l1, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -1273,7 +1327,7 @@ static di_status refine_pass(di_graph_s *g, di_state_s *st, cudaStream_t s)
     launch_plan(g, st, w, s, 0, cudaGraphConditionalHandle{});
     launch_push(g, st, w, s);
     k_reduce<<<(unsigned)st->ntiles, SEL_THREADS, 0, s>>>(st->F, nullptr, static_cast<const Off *>(g->rp), g->n,
-                                                          st->ntiles, st->tile_l1, st->tile_l, st->ctl, RED_CYCLE,
+                                                          st->ntiles, st->tile_l1, st->tile_l, st->tile_max, st->ctl, RED_CYCLE,
                                                           st->F32);
     count_launches(1);
     DI_CUDA(cudaGetLastError());
@@ -1283,7 +1337,7 @@ static di_status refine_pass(di_graph_s *g, di_state_s *st, cudaStream_t s)
 constexpr int MAX_CYCLES = 64;   // FP32-form cycles per call (each gains >= 1/refine_ratio)
 
 di_status solve_loop(di_graph_s *g, di_state_s *st, double tol, const di_opts *o, di_info *info,
-                     cudaStream_t s, bool fresh, const double *Z_dev)
+                     cudaStream_t s, bool fresh, const double *Z_dev, bool inf_norm)
 {
     const int64_t n = g->n;
     const double d = st->d;
@@ -1306,9 +1360,11 @@ di_status solve_loop(di_graph_s *g, di_state_s *st, double tol, const di_opts *o
     hc->stop_l1 = (1.0 - d) * tol;
     hc->refine_ratio = o->refine_ratio;
     hc->max_sweeps = (unsigned long long)o->max_sweeps;
+    hc->inf_norm = inf_norm ? 1 : 0;
+    hc->inf_cap = 0.5 * (1.0 - d);
     DI_CUDA(cudaMemcpyAsync(st->ctl, hc, sizeof(DevCtl), cudaMemcpyHostToDevice, s));
     k_reduce<<<(unsigned)st->ntiles, SEL_THREADS, 0, s>>>(st->F, nullptr, static_cast<const Off *>(g->rp),
-                                                          n, st->ntiles, st->tile_l1, st->tile_l,
+                                                          n, st->ntiles, st->tile_l1, st->tile_l, st->tile_max,
                                                           st->ctl, f32 ? RED_CYCLE : RED_INIT,
                                                           f32 ? st->F32 : nullptr);
     count_launches(1);
@@ -1347,7 +1403,7 @@ di_status solve_loop(di_graph_s *g, di_state_s *st, double tol, const di_opts *o
     DI_CUDA(cudaEventRecord(st->ev1, s));
     const unsigned done = hc->done;   // (graph mode: read below)
     k_reduce<<<(unsigned)st->ntiles, SEL_THREADS, 0, s>>>(st->F, st->H, static_cast<const Off *>(g->rp),
-                                                          n, st->ntiles, st->tile_l1, st->tile_l,
+                                                          n, st->ntiles, st->tile_l1, st->tile_l, st->tile_max,
                                                           st->ctl, RED_FINAL, nullptr);
     count_launches(1);
     DI_CUDA(cudaGetLastError());
@@ -1388,6 +1444,8 @@ di_status solve_loop(di_graph_s *g, di_state_s *st, double tol, const di_opts *o
         info->push_entries = push_entries;
         info->refinements = refinements;
         info->refine_links = refine_links;
+        info->resid_inf = hc->final_max;
+        if (inf_norm) info->bound = hc->final_max / (1.0 - d);
     }
     if (hc->err) return DI_ERR_DEVICE_TIMEOUT;
     if (hc->done == 2) return DI_ERR_NOT_CONVERGED;
@@ -1446,7 +1504,7 @@ di_status state_l(di_graph_s *g, di_state_s *st, double *l, cudaStream_t s)
     DI_TRY(t.get(&ctl, 1));
     DI_CUDA(cudaMemsetAsync(ctl, 0, sizeof(DevCtl), s));
     k_reduce<<<(unsigned)st->ntiles, SEL_THREADS, 0, s>>>(st->F, st->H, static_cast<const Off *>(g->rp),
-                                                          g->n, st->ntiles, st->tile_l1, st->tile_l, ctl,
+                                                          g->n, st->ntiles, st->tile_l1, st->tile_l, nullptr, ctl,
                                                           RED_FINAL, nullptr);
     count_launches(1);
     DI_CUDA(cudaGetLastError());

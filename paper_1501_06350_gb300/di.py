@@ -224,3 +224,72 @@ def residual_l1(graph: Graph, v) -> float:
     L.check(L.lib().di_residual_l1(graph.handle, _p(v), ctypes.byref(out), mem, _stream()),
             "di_residual_l1")
     return out.value
+
+
+def adjoint(graph: Graph, d: float, g, x=None, tol: float = 1e-12, device: bool = True, want_grad_w: bool = True,
+            **opts):
+    """Backward pass of the solve for L = g . x: lambda with (I - d P)^T lambda = g,
+    dL/dZ = (1 - d) lambda and dL/dw per link of the canonical out-CSR (needs the
+    forward solution x).  Returns (lambda, grad_Z, grad_w or None, info)."""
+    mem = L.DI_MEM_DEVICE if device else L.DI_MEM_HOST
+    g = _prep(g, np.float64, _f64, mem)
+    x = _prep(x, np.float64, _f64, mem)
+    n = graph.n
+    lam = _out_buffer(n, device)
+    gz = _out_buffer(n, device)
+    gw = _out_buffer(max(graph.nnz, 1), device) if (want_grad_w and x is not None) else None
+    info = L.di_info()
+    o = L.default_opts(**opts)
+    rc = L.lib().di_adjoint(graph.handle, d, _p(g), _p(x), tol, ctypes.byref(o), _p(lam), _p(gz), _p(gw),
+                            ctypes.byref(info), mem, _stream())
+    if rc not in (L.DI_OK, L.DI_ERR_NOT_CONVERGED):
+        raise L.DIError(rc, "di_adjoint")
+    out = info.as_dict()
+    out["converged"] = rc == L.DI_OK
+    return lam, gz, (None if gw is None else gw[:graph.nnz]), out
+
+
+class PageRank(torch.autograd.Function):
+    """x = (1 - d)(I - d P(w))^-1 Z with gradients for the link weights w and Z.
+
+    forward(w, Z, n, ptr, idx, d, tol, adj_tol): ``ptr``/``idx`` a canonical
+    out-CSR (rows sorted by target, no repeated link; e.g. from
+    ``Graph.export_csr``) so that ``w`` (CUDA, one weight per link, > 0) is in
+    the library's link order; ``Z`` a CUDA vector of n values.  The forward runs
+    ``di_solve`` to ``tol``; the backward runs ``di_adjoint`` to ``adj_tol`` on
+    the same graph.  x is float64; the gradients come back in the dtypes of w
+    and Z.
+    """
+
+    @staticmethod
+    def forward(ctx, w, Z, n, ptr, idx, d=0.85, tol=1e-12, adj_tol=1e-12):
+        G = Graph(n, ptr, idx, w.detach())
+        p, i, _ = G.export_csr(device=True, weights=False)
+        if not (torch.equal(p.to(torch.int64), ptr.to(p.device, torch.int64))
+                and torch.equal(i, idx.to(i.device, torch.int32))):
+            raise ValueError("PageRank needs a canonical out-CSR (sorted rows, no repeated link)")
+        st = State(G)
+        x, info = st.solve(d, Z=Z.detach().to(_f64), tol=tol)
+        if not info["converged"]:
+            raise RuntimeError(f"di_solve did not converge: {info}")
+        ctx.graph, ctx.d, ctx.adj_tol = G, d, adj_tol
+        ctx.wdt, ctx.zdt = w.dtype, Z.dtype
+        ctx.save_for_backward(x)
+        st.close()
+        return x
+
+    @staticmethod
+    def backward(ctx, gx):
+        (x,) = ctx.saved_tensors
+        lam, gz, gw, info = adjoint(ctx.graph, ctx.d, gx.detach().to(_f64).contiguous(), x, tol=ctx.adj_tol,
+                                    want_grad_w=ctx.needs_input_grad[0])
+        if not info["converged"]:
+            raise RuntimeError(f"di_adjoint did not converge: {info}")
+        gw_out = gw.to(ctx.wdt) if gw is not None else None
+        gz_out = gz.to(ctx.zdt) if ctx.needs_input_grad[1] else None
+        return gw_out, gz_out, None, None, None, None, None, None
+
+
+def pagerank(w, Z, n, ptr, idx, d=0.85, tol=1e-12, adj_tol=1e-12):
+    """Differentiable solve: see PageRank."""
+    return PageRank.apply(w, Z, n, ptr, idx, d, tol, adj_tol)
