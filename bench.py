@@ -156,6 +156,40 @@ def cpu_baseline(g, cp, ci):
             "time_to_tol_s": dt, "edge_pushes": info["edge_pushes"], "diffusions": info["diffusions"]}
 
 
+def adjoint_leg(torch, di, reps=4):
+    """Backward pass on the weighted 2M-page / 20M-link web graph (lognormal(0,1)
+    FP32 weights): forward solve to tol, then lambda with |lambda - H|_inf <= tol,
+    dL/dZ and dL/dw for L = g . x, g ~ N(0,1).  Device times (CUDA events)."""
+    ga = synth.cached(synth.web_graph, n=2_000_000, m_target=20_000_000, weighted="lognormal32",
+                      seed_offset=4)
+    G = di.Graph(ga.n, ga.ptr, ga.idx, ga.w)
+    gv = torch.from_numpy(synth.rng_for(41).standard_normal(ga.n)).cuda()
+    x, xi, st = di.solve(G, D, tol=TOL)
+    fwd, bwd, info = [], [], None
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    for k in range(reps + 1):
+        ev[0].record()
+        x, xi = st.solve(D, tol=TOL)
+        ev[1].record()
+        lam, gz, gw, info = di.adjoint(G, D, gv, x, tol=TOL)
+        ev[2].record()
+        torch.cuda.synchronize()
+        if k:
+            fwd.append(ev[0].elapsed_time(ev[1]))
+            bwd.append(ev[1].elapsed_time(ev[2]))
+    gi = G.info()
+    out = {"workload": "web-like graph, 2,000,000 pages, 20,000,000 links, lognormal(0,1) FP32 weights, "
+                       "d=0.85; L = g.x with g ~ N(0,1)",
+           "links": gi["nnz"], "forward_ms": statistics.median(fwd), "backward_ms": statistics.median(bwd),
+           "backward_includes": "adjoint diffusion to |lambda-H|_inf <= 1e-9, dL/dZ, dL/dw (all links)",
+           "adjoint_sweeps": info["sweeps"], "adjoint_edge_pushes": info["edge_pushes"],
+           "adjoint_edge_pushes_per_s": info["edge_pushes"] / (info["time_ms"] / 1e3),
+           "adjoint_solve_ms": info["time_ms"], "bound_inf": info["bound"]}
+    st.close()
+    G.close()
+    return out
+
+
 def oracle_x(g, cp, ci):
     """The oracle's x to 1e-12 (|F|_1/(1-d)), to state each form's error."""
     import oracle
@@ -217,6 +251,8 @@ def main():
                          "history and FP64 residual refinement")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the side-by-side time to tol of both forms")
+    ap.add_argument("--no-adjoint", action="store_true",
+                    help="skip the backward-pass timing on the 2M-page weighted graph")
     args = ap.parse_args()
     if args.warmup < 3 and not args.small:
         ap.error("--warmup must be >= 3")
@@ -353,6 +389,10 @@ def main():
         x_ref = oracle_x(g, cp, ci)
     if rank == 0 and not args.no_forms:
         out["forms"] = forms(st, G, g, torch, x_ref)
+    if rank == 0 and not args.no_adjoint:
+        st.close()
+        G.close()
+        out["adjoint"] = adjoint_leg(torch, di)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:

@@ -38,13 +38,13 @@ di_status dalloc_t(T **p, size_t count, cudaStream_t s)
 // RAII holder for temporaries of one call (freed stream-ordered).
 struct Temps {
     cudaStream_t s;
-    void *p[32];
+    void *p[64];
     int k = 0;
     explicit Temps(cudaStream_t st) : s(st) {}
     template <typename T>
     di_status get(T **out, size_t count)
     {
-        if (k >= 32) return DI_ERR_OOM;
+        if (k >= 64) return DI_ERR_OOM;
         di_status r = dalloc_t(out, count, s);
         if (r == DI_OK) p[k++] = *out;
         return r;

@@ -181,77 +181,150 @@ __device__ __forceinline__ int64_t lower_key(const uint64_t *ukey, int64_t nu, u
     return lo;
 }
 
-// A changed row: merge its old links with its batch entries (both sorted by
-// target).  Also W_j of the new row (left to right) and the dangling change.
-__global__ void k_merge_rows(const uint32_t *tlist, int64_t nt, const Off *rp, const int32_t *col, const double *w,
-                             const Off *nrp, const uint64_t *ukey, const uint8_t *eff, const double *uw, int64_t nu,
-                             int32_t *ncol, double *nw, double *nwsum, long long *ddang)
+// Changed rows are cut into chunks of CH old links (a row without old links
+// is one chunk), so that a long row is merged and injected by many threads.
+constexpr Off CH = 256;
+
+__global__ void k_chunk_counts(const uint32_t *tlist, int64_t nt, const Off *rp, uint32_t *cnt)
+{
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nt;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t j = tlist[k];
+        const Off deg = rp[j + 1] - rp[j];
+        cnt[k] = deg == 0 ? 1u : (uint32_t)((deg + CH - 1) / CH);
+    }
+}
+
+__global__ void k_chunk_fill(const uint32_t *cnt, const uint64_t *cpos, int64_t nt, uint32_t *ch_row,
+                             uint32_t *ch_idx)
+{
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nt;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t base = cpos[k];
+        for (uint32_t c = 0; c < cnt[k]; c++) {
+            ch_row[base + c] = (uint32_t)k;
+            ch_idx[base + c] = c;
+        }
+    }
+}
+
+// First batch entry of row j whose target is >= t, inside [q, qe).
+__device__ __forceinline__ int64_t lower_target(const uint64_t *ukey, int64_t q, int64_t qe, uint64_t key)
+{
+    while (q < qe) {
+        const int64_t mid = (q + qe) >> 1;
+        if (ukey[mid] < key) q = mid + 1;
+        else qe = mid;
+    }
+    return q;
+}
+
+// One chunk of a changed row: its old links [c CH, (c+1) CH) merged with the
+// row's batch entries whose targets fall in the chunk's target range (from
+// the chunk's first target up to the next chunk's first target; the first
+// and last chunks are open-ended).  The output position of the chunk's first
+// element is its old position minus the deletions and plus the insertions
+// listed before it (ins_pre / del_pre: exclusive prefix counts over the
+// sorted batch).
+__global__ void k_merge_chunks(const uint32_t *ch_row, const uint32_t *ch_idx, int64_t nch, const uint32_t *tlist,
+                               const Off *rp, const int32_t *col, const double *w, const Off *nrp,
+                               const uint64_t *ukey, const uint8_t *eff, const double *uw, int64_t nu,
+                               const uint64_t *ins_pre, const uint64_t *del_pre, int32_t *ncol, double *nw)
+{
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nch;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t j = tlist[ch_row[t]];
+        const Off c = ch_idx[t];
+        const Off a = rp[j], b = rp[j + 1];
+        const int64_t q = lower_key(ukey, nu, (uint64_t)j << 32);
+        const int64_t qe = lower_key(ukey, nu, (uint64_t)(j + 1) << 32);
+        const Off i0 = a + c * CH;
+        const Off i1 = (b - i0 > CH) ? i0 + CH : b;
+        const uint64_t rowkey = (uint64_t)j << 32;
+        const int64_t q0 = c == 0 ? q : lower_target(ukey, q, qe, rowkey | (uint32_t)col[i0]);
+        const int64_t q1 = i1 == b ? qe : lower_target(ukey, q, qe, rowkey | (uint32_t)col[i1]);
+        Off out = nrp[j] + (i0 - a) - (Off)(del_pre[q0] - del_pre[q]) + (Off)(ins_pre[q0] - ins_pre[q]);
+        Off i = i0;
+        int64_t k = q0;
+        while (i < i1 || k < q1) {
+            const int64_t to = i < i1 ? (int64_t)col[i] : INT64_MAX;
+            const int64_t tb = k < q1 ? (int64_t)(uint32_t)ukey[k] : INT64_MAX;
+            int32_t cc = -1;
+            double x = 1.0;
+            if (to < tb) {
+                cc = (int32_t)to;
+                x = w ? w[i] : 1.0;
+                i++;
+            } else if (to == tb) {
+                const unsigned char e = eff[k];
+                if (e != EFF_DEL) {
+                    cc = (int32_t)to;
+                    x = e == EFF_UPD ? uw[k] : (w ? w[i] : 1.0);
+                }
+                i++;
+                k++;
+            } else {
+                if (eff[k] == EFF_INS) {
+                    cc = (int32_t)tb;
+                    x = uw[k];
+                }
+                k++;
+            }
+            if (cc >= 0) {
+                ncol[out] = cc;
+                if (nw) nw[out] = x;
+                out++;
+            }
+        }
+    }
+}
+
+// Per changed row: W_j of the new row (left to right, as at creation) and the
+// change in the number of dangling nodes.
+__global__ void k_row_finish(const uint32_t *tlist, int64_t nt, const Off *rp, const Off *nrp, const double *nw,
+                             double *nwsum, long long *ddang)
 {
     long long dd = 0;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nt;
          k += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t j = tlist[k];
-        int64_t q = lower_key(ukey, nu, (uint64_t)j << 32);
-        const int64_t qe = lower_key(ukey, nu, (uint64_t)(j + 1) << 32);
-        Off i = rp[j];
-        const Off b = rp[j + 1];
-        Off out = nrp[j];
-        double ws = 0.0;
-        bool first = true;
-        while (i < b || q < qe) {
-            const int64_t to = i < b ? (int64_t)col[i] : INT64_MAX;
-            const int64_t tb = q < qe ? (int64_t)(uint32_t)ukey[q] : INT64_MAX;
-            int32_t c = -1;
-            double x = 1.0;
-            if (to < tb) {
-                c = (int32_t)to;
-                x = w ? w[i] : 1.0;
-                i++;
-            } else if (to == tb) {
-                const unsigned char e = eff[q];
-                if (e != EFF_DEL) {
-                    c = (int32_t)to;
-                    x = e == EFF_UPD ? uw[q] : (w ? w[i] : 1.0);
-                }
-                i++;
-                q++;
-            } else {
-                if (eff[q] == EFF_INS) {
-                    c = (int32_t)tb;
-                    x = uw[q];
-                }
-                q++;
-            }
-            if (c >= 0) {
-                ncol[out] = c;
-                if (nw) {
-                    nw[out] = x;
-                    ws = first ? x : ws + x;
-                    first = false;
-                }
-                out++;
-            }
+        if (nwsum) {
+            double ws = 0.0;
+            for (Off e = nrp[j]; e < nrp[j + 1]; e++) ws = e == nrp[j] ? nw[e] : ws + nw[e];
+            nwsum[j] = ws;
         }
-        if (nwsum) nwsum[j] = ws;
         const bool was = rp[j + 1] == rp[j], now = nrp[j + 1] == nrp[j];
         dd += (long long)now - (long long)was;
     }
     if (dd) atomicAdd((unsigned long long *)ddang, (unsigned long long)dd);
 }
 
-// F += sign * d H_j P[:, j] for the listed columns (one warp per column).
-__global__ void k_inject_list(const uint32_t *tlist, int64_t nt, const Off *rp, const int32_t *col, const double *w,
-                              const double *wsum, const double *H, double sd, double *F)
+__global__ void k_flags(const uint8_t *eff, int64_t nu, uint8_t *ins, uint8_t *del)
+{
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nu;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        ins[k] = eff[k] == EFF_INS;
+        del[k] = eff[k] == EFF_DEL;
+    }
+}
+
+// F += sign * d H_j P[:, j] for the listed columns, one warp per chunk of CH
+// links of a column.
+__global__ void k_inject_chunks(const uint32_t *ch_row, const uint32_t *ch_idx, int64_t nch, const uint32_t *tlist,
+                                const Off *rp, const int32_t *col, const double *w, const double *wsum,
+                                const double *H, double sd, double *F)
 {
     const int lane = threadIdx.x & 31;
     const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < nt; k += nwarp) {
-        const uint32_t j = tlist[k];
+    for (int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < nch; t += nwarp) {
+        const uint32_t j = tlist[ch_row[t]];
         const Off a = rp[j], b = rp[j + 1];
-        if (a == b) continue;
+        const Off i0 = a + ch_idx[t] * CH;
+        if (i0 >= b) continue;
+        const Off i1 = (b - i0 > CH) ? i0 + CH : b;
         const double h = sd * H[j];
         const double unit = w ? h / wsum[j] : h / (double)(b - a);
-        for (Off e = a + lane; e < b; e += 32) atomicAdd(F + col[e], w ? unit * w[e] : unit);
+        for (Off e = i0 + lane; e < i1; e += 32) atomicAdd(F + col[e], w ? unit * w[e] : unit);
     }
 }
 
@@ -365,17 +438,60 @@ di_status update_edges(di_graph_s *g, di_state_s *st, int64_t m, const int32_t *
     DI_CUDA(cudaMemsetAsync(ddang, 0, sizeof(long long), s));
     k_list<<<grid_for(n, 256), 256, 0, s>>>(touched, tpos, n, tlist);
     count_launches(1);
-    k_merge_rows<<<grid_for((int64_t)nt, 128), 128, 0, s>>>(tlist, (int64_t)nt, rp, g->col, g->w, nrp, ukey, eff,
-                                                            uw, (int64_t)nu, ncol, nwv, nwsum, ddang);
+    // insertions / deletions before each batch entry (exclusive counts)
+    uint8_t *fins, *fdel;
+    uint64_t *ins_pre, *del_pre;
+    DI_TRY(t.get(&fins, nu + 1));
+    DI_TRY(t.get(&fdel, nu + 1));
+    DI_TRY(t.get(&ins_pre, nu + 1));
+    DI_TRY(t.get(&del_pre, nu + 1));
+    DI_CUDA(cudaMemsetAsync(fins + nu, 0, 1, s));
+    DI_CUDA(cudaMemsetAsync(fdel + nu, 0, 1, s));
+    k_flags<<<grid_for((int64_t)nu, 256), 256, 0, s>>>(eff, (int64_t)nu, fins, fdel);
+    count_launches(1);
+    DI_TRY(scan_exclusive<uint8_t>(fins, ins_pre, (int64_t)nu + 1, nullptr, s));
+    DI_TRY(scan_exclusive<uint8_t>(fdel, del_pre, (int64_t)nu + 1, nullptr, s));
+    // chunks of the changed rows, old and new
+    uint32_t *ocnt, *ncnt;
+    uint64_t *ocpos, *ncpos, *ototal, *ntotal;
+    DI_TRY(t.get(&ocnt, nt + 1));
+    DI_TRY(t.get(&ncnt, nt + 1));
+    DI_TRY(t.get(&ocpos, nt + 1));
+    DI_TRY(t.get(&ncpos, nt + 1));
+    DI_TRY(t.get(&ototal, 1));
+    DI_TRY(t.get(&ntotal, 1));
+    k_chunk_counts<<<grid_for((int64_t)nt, 256), 256, 0, s>>>(tlist, (int64_t)nt, rp, ocnt);
+    k_chunk_counts<<<grid_for((int64_t)nt, 256), 256, 0, s>>>(tlist, (int64_t)nt, nrp, ncnt);
+    count_launches(2);
+    DI_TRY(scan_exclusive<uint32_t>(ocnt, ocpos, (int64_t)nt, ototal, s));
+    DI_TRY(scan_exclusive<uint32_t>(ncnt, ncpos, (int64_t)nt, ntotal, s));
+    uint64_t hch[2] = {0, 0};
+    DI_CUDA(cudaMemcpyAsync(hch, ototal, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+    DI_CUDA(cudaMemcpyAsync(hch + 1, ntotal, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+    DI_CUDA(cudaStreamSynchronize(s));
+    uint32_t *och_row, *och_idx, *nch_row, *nch_idx;
+    DI_TRY(t.get(&och_row, hch[0] + 1));
+    DI_TRY(t.get(&och_idx, hch[0] + 1));
+    DI_TRY(t.get(&nch_row, hch[1] + 1));
+    DI_TRY(t.get(&nch_idx, hch[1] + 1));
+    k_chunk_fill<<<grid_for((int64_t)nt, 256), 256, 0, s>>>(ocnt, ocpos, (int64_t)nt, och_row, och_idx);
+    k_chunk_fill<<<grid_for((int64_t)nt, 256), 256, 0, s>>>(ncnt, ncpos, (int64_t)nt, nch_row, nch_idx);
+    count_launches(2);
+    k_merge_chunks<<<grid_for((int64_t)hch[0], 128), 128, 0, s>>>(och_row, och_idx, (int64_t)hch[0], tlist, rp, g->col,
+                                                                   g->w, nrp, ukey, eff, uw, (int64_t)nu, ins_pre,
+                                                                   del_pre, ncol, nwv);
+    count_launches(1);
+    k_row_finish<<<grid_for((int64_t)nt, 128), 128, 0, s>>>(tlist, (int64_t)nt, rp, nrp, nwv, nwsum, ddang);
     count_launches(1);
     // 6. F += d (P' - P) H: withdraw the old columns, inject the new ones
     if (st && nt) {
-        k_inject_list<<<grid_for((int64_t)nt * 32, 256), 256, 0, s>>>(tlist, (int64_t)nt, rp, g->col, g->w, g->wsum,
-                                                                      st->H, -st->d, st->F);
-        count_launches(1);
-        k_inject_list<<<grid_for((int64_t)nt * 32, 256), 256, 0, s>>>(tlist, (int64_t)nt, nrp, ncol, nwv, nwsum,
-                                                                      st->H, st->d, st->F);
-        count_launches(1);
+        k_inject_chunks<<<grid_for((int64_t)hch[0] * 32, 256), 256, 0, s>>>(och_row, och_idx, (int64_t)hch[0], tlist,
+                                                                          rp, g->col, g->w, g->wsum, st->H,
+                                                                          -st->d, st->F);
+        k_inject_chunks<<<grid_for((int64_t)hch[1] * 32, 256), 256, 0, s>>>(nch_row, nch_idx, (int64_t)hch[1], tlist,
+                                                                          nrp, ncol, nwv, nwsum, st->H, st->d,
+                                                                          st->F);
+        count_launches(2);
     }
     DI_CUDA(cudaGetLastError());
     long long hd = 0;
