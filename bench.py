@@ -348,8 +348,14 @@ def main():
     _, prof = st.solve(D, tol=TOL, profile=1, **sopt)
     per_launch_links = prof["push_edges"] / max(prof["push_launches"], 1)
     push_avg_s = prof["push_ms"] / 1e3 / max(prof["push_launches"], 1)
-    link_bytes = 8.0 if args.precision == "f32" else 12.0   # 4 B target + the fluid word added
-    alg_bytes = link_bytes * per_launch_links
+    # algorithmic bytes per launch: per pushed link the 4 B target and the fluid
+    # word added at the target; per diffused node 8 B of row pointers, the
+    # fluid word taken (read + write), 16 B history read + write (FP64 H, or
+    # the FP64 cycle accumulator), 8 B d/W_j and 4 B of frontier
+    link_bytes = 8.0 if args.precision == "f32" else 12.0
+    node_bytes = 36.0 if args.precision == "f32" else 44.0
+    per_launch_nodes = prof["push_entries"] / max(prof["push_launches"], 1)
+    alg_bytes = link_bytes * per_launch_links + node_bytes * per_launch_nodes
     peaks = {}
     pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(pk_path):
@@ -360,7 +366,8 @@ def main():
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "kernel": "k_push<float>" if args.precision == "f32" else "k_push<double>",
-                "bytes_per_link": link_bytes,
+                "bytes_per_link": link_bytes, "bytes_per_node": node_bytes,
+                "nodes_per_launch": per_launch_nodes,
                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
                 "algorithmic_bytes_per_launch": alg_bytes, "links_per_launch": per_launch_links,
                 "launches": prof["push_launches"], "push_ms_avg": 1e3 * push_avg_s,
