@@ -202,6 +202,36 @@ di_status di_state_import(di_state_t s, const double *H, const double *F, double
                           void *stream);
 
 /* ---------------------------------------------------------------------------
+ * Batched personalised solves: B teleport vectors on one graph (topic-
+ * sensitive PageRank, Section 2.1; DI of Section 3.1 for each column).
+ *
+ * Solves x_c = d P x_c + (1 - d) Z_c for c = 0 .. B-1 together.  The fluid of
+ * all columns of a node is stored contiguously, so one read of a node's links
+ * serves every column and one link adds B contiguous values.  Each column has
+ * its own DI-argmax threshold (Section 3.4) and stop test
+ * |F_c|_1 / (1 - d) <= tol (Theorem 1); a node is diffused (all its columns)
+ * when one of its unconverged columns passes its threshold.  Arithmetic as
+ * DI_PREC_F32 of di_solve: FP32 fluid in the sweeps, FP64 accumulation of the
+ * taken fluid, and cycles ended by an FP64 refinement R = R + d P D - D
+ * (Eq. HnFn, computed by a pull over the in-links) on which the stop test is
+ * applied, so every column's bound is certified in FP64.
+ *   B        1 <= B <= 64 (fewer than 64 columns are padded internally)
+ *   d        0 < d < 1
+ *   Z        float64[n][B] in `mem`, node-major (Z[i*B + c]); finite; NULL = every
+ *            column uniform 1/n
+ *   tol      > 0, for every column
+ *   opts     NULL = defaults; theta_factor, max_sweeps, use_graph, check_every and
+ *            refine_ratio apply; precision and profile are ignored
+ *   H_out    float64[n][B] in `mem` (node-major) or NULL
+ *   resid_out float64[B] in `mem` or NULL: |F_c|_1 of each column's returned
+ *            state (exact FP64 sum in a fixed order)
+ *   info     may be NULL; resid_l1 / bound are those of the worst column
+ * Temporary device memory: about n x 64 x 36 bytes plus the graph's reverse
+ * structure (kept with the graph).  DI_ERR_NOT_CONVERGED: sweep cap reached. */
+di_status di_solve_batch(di_graph_t g, int32_t B, double d, const double *Z, double tol, const di_opts *opts,
+                         double *H_out, double *resid_out, di_info *info, int mem, void *stream);
+
+/* ---------------------------------------------------------------------------
  * Adjoint (backward pass of the solve; the paper has no counterpart).
  *
  * For a loss L = g . x with x = (1 - d)(I - d P)^-1 Z (Section 2.1,

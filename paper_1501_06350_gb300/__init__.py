@@ -8,7 +8,8 @@ first call that needs libdi.so loads it and fails loudly when it is missing.
 """
 import importlib
 
-__all__ = ["Graph", "State", "solve", "frontier_select", "residual_l1", "adjoint", "PageRank", "pagerank"]
+__all__ = ["Graph", "State", "solve", "solve_batch", "frontier_select", "residual_l1", "adjoint", "PageRank",
+           "pagerank"]
 
 
 def __getattr__(name):

@@ -88,6 +88,8 @@ SIGNATURES = {
     "di_update_edges": (INT, [P, P, I64, P, P, P, P, INT, P]),
     "di_state_export": (INT, [P, P, P, P, INT, P]),
     "di_state_import": (INT, [P, P, P, ctypes.c_double, INT, P]),
+    "di_solve_batch": (INT, [P, ctypes.c_int32, ctypes.c_double, P, ctypes.c_double, ctypes.POINTER(di_opts),
+                             P, P, ctypes.POINTER(di_info), INT, P]),
     "di_adjoint": (INT, [P, ctypes.c_double, P, P, ctypes.c_double, ctypes.POINTER(di_opts), P, P, P,
                          ctypes.POINTER(di_info), INT, P]),
     "di_frontier_select": (INT, [P, P, ctypes.c_double, P, ctypes.POINTER(I64), INT, P]),

@@ -333,6 +333,30 @@ di_status di_state_import(di_state_t st, const double *H, const double *F, doubl
     return DI_OK;
 }
 
+di_status di_solve_batch(di_graph_t g, int32_t B, double d, const double *Z, double tol, const di_opts *opts,
+                         double *H_out, double *resid_out, di_info *info, int mem, void *stream)
+{
+    if (!g || !mem_ok(mem) || B < 1 || B > 64) return DI_ERR_INVALID_ARG;
+    if (!(d > 0.0 && d < 1.0) || !(tol > 0.0) || !isfinite(tol)) return DI_ERR_INVALID_ARG;
+    di_opts o;
+    di_opts_default(&o);
+    if (opts) o = *opts;
+    o.precision = DI_PREC_F32;
+    o.profile = 0;
+    DI_TRY(opts_ok(&o));
+    DeviceScope ds(g->device);
+    cudaStream_t s = as_stream(stream);
+    Temps t(s);
+    const double *Zd = nullptr;
+    DI_TRY(stage_in(Z, g->n * (int64_t)B, mem, t, &Zd, s));
+    if (Zd) {
+        bool ok = false;
+        DI_TRY(check_finite(Zd, g->n * (int64_t)B, &ok, s));
+        if (!ok) return DI_ERR_INVALID_ARG;
+    }
+    return solve_batch(g, B, d, Zd, tol, &o, H_out, resid_out, info, mem, s);
+}
+
 di_status di_adjoint(di_graph_t g, double d, const double *gvec, const double *x, double tol, const di_opts *opts,
                      double *lambda_out, double *grad_Z_out, double *grad_w_out, di_info *info, int mem,
                      void *stream)

@@ -230,6 +230,8 @@ di_status solve_loop(di_graph_s *g, di_state_s *st, double tol, const di_opts *o
                      cudaStream_t s, bool fresh, const double *Z_dev, bool inf_norm = false);
 di_status graph_build_reverse(di_graph_s *g, cudaStream_t s);
 void reverse_release(di_graph_s *g);
+di_status solve_batch(di_graph_s *g, int B, double d, const double *Z, double tol, const di_opts *o, double *H_out,
+                      double *resid_out, di_info *info, int mem, cudaStream_t s);
 di_status adjoint(di_graph_s *g, double d, const double *gvec, const double *x, double tol, const di_opts *o,
                   double *lambda, double *grad_Z, double *grad_w, di_info *info, cudaStream_t s);
 di_status l1_device(di_graph_s *g, const double *v, double *out_host, cudaStream_t s);

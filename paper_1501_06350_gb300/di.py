@@ -293,3 +293,31 @@ class PageRank(torch.autograd.Function):
 def pagerank(w, Z, n, ptr, idx, d=0.85, tol=1e-12, adj_tol=1e-12):
     """Differentiable solve: see PageRank."""
     return PageRank.apply(w, Z, n, ptr, idx, d, tol, adj_tol)
+
+
+def solve_batch(graph: Graph, Z, d: float = 0.85, tol: float = 1e-9, device: bool = True, **opts):
+    """B personalised solves at once (Z: n x B, node-major, B <= 64).  Returns
+    (H as n x B, per-column |F_c|_1, info)."""
+    mem = L.DI_MEM_DEVICE if device else L.DI_MEM_HOST
+    if isinstance(Z, torch.Tensor):
+        B = int(Z.shape[1])
+    else:
+        Z = np.asarray(Z)
+        B = int(Z.shape[1])
+    Zp = _prep(Z.reshape(-1) if not isinstance(Z, torch.Tensor) else Z.reshape(-1), np.float64, _f64, mem)
+    n = graph.n
+    if device:
+        H = torch.empty((n, B), dtype=_f64, device="cuda")
+        res = torch.empty(B, dtype=_f64, device="cuda")
+    else:
+        H = np.empty((n, B), dtype=np.float64)
+        res = np.empty(B, dtype=np.float64)
+    info = L.di_info()
+    o = L.default_opts(**opts)
+    rc = L.lib().di_solve_batch(graph.handle, B, d, _p(Zp), tol, ctypes.byref(o), _p(H), _p(res),
+                                ctypes.byref(info), mem, _stream())
+    if rc not in (L.DI_OK, L.DI_ERR_NOT_CONVERGED):
+        raise L.DIError(rc, "di_solve_batch")
+    out = info.as_dict()
+    out["converged"] = rc == L.DI_OK
+    return H, res, out

@@ -293,6 +293,49 @@ def seed_set_z(n: int, n_seeds: int, seed_offset: int) -> np.ndarray:
     return z
 
 
+def seed_set_batch(n: int, B: int, seed_offset: int, max_seeds: int = 1000) -> np.ndarray:
+    """B personalised teleport vectors as an n x B node-major matrix: column c is
+    uniform over a random set of 1 .. max_seeds seed pages."""
+    rng = rng_for(3500 + seed_offset)
+    Z = np.zeros((n, B), dtype=np.float64)
+    for c in range(B):
+        k = int(rng.integers(1, max_seeds + 1))
+        k = min(k, n)
+        Z[rng.choice(n, size=k, replace=False), c] = 1.0 / k
+    return Z
+
+
+def small_web_graphs(count: int, n_lo: int, n_hi: int, avg_deg: float, seed_offset: int) -> list:
+    """``count`` independent host-structured graphs with sizes uniform in
+    [n_lo, n_hi] and about ``avg_deg`` links per page."""
+    rng = rng_for(5000 + seed_offset)
+    out = []
+    for k in range(count):
+        nk = int(rng.integers(n_lo, n_hi + 1))
+        out.append(web_graph(n=nk, m_target=int(avg_deg * nk), seed_offset=6000 + seed_offset * 1000 + k,
+                             deg_hi=min(50_000, nk - 1)))
+    return out
+
+
+def union(graphs: list) -> tuple:
+    """Block-diagonal union of independent graphs (node ids offset graph by
+    graph) and the node offsets; the teleport vector that is uniform on each
+    component (1/n_k on graph k)."""
+    offs = np.zeros(len(graphs) + 1, dtype=np.int64)
+    for k, g in enumerate(graphs):
+        offs[k + 1] = offs[k] + g.n
+    n = int(offs[-1])
+    ptr = np.zeros(n + 1, dtype=np.int64)
+    idx_parts = []
+    for k, g in enumerate(graphs):
+        ptr[offs[k] + 1:offs[k + 1] + 1] = np.diff(g.ptr)
+        idx_parts.append(g.idx.astype(np.int64) + offs[k])
+    ptr = np.cumsum(ptr)
+    idx = np.concatenate(idx_parts).astype(np.int32) if idx_parts else np.zeros(0, np.int32)
+    Z = np.concatenate([np.full(g.n, 1.0 / g.n) for g in graphs])
+    return RawGraph(n, ptr, idx, None, {"components": len(graphs)}), offs, Z
+
+
 def edge_batch(g_canon_ptr: np.ndarray, g_canon_idx: np.ndarray, n: int, frac: float,
                seed_offset: int, insert_share: float = 0.5) -> tuple[np.ndarray, np.ndarray, np.ndarray]:
     """Random link changes: ``frac`` of the current links, half deletions of existing
