@@ -11,18 +11,23 @@
 // active columns passes, and then all its columns are diffused (any amount is
 // a valid diffusion of Eq. defF).
 //
-// Precision as in the FP32 form of the single solve: the sweeps move FP32
-// fluid and add the taken fluid exactly to an FP64 accumulator D; a cycle ends
-// per column at refine_ratio x its starting |F_c|_1, then the FP64 fluid R
-// becomes R + d P D - D (Eq. HnFn, computed by a pull over the in-links of
-// every node: deterministic, no atomics except for rows split across warps),
-// H += D, and the stop test is applied to the exact FP64 |R_c|_1.
+// Precision: the sweeps move FP32 fluid and add the taken fluid to an FP32
+// accumulator D; a cycle ends per column at refine_ratio x its starting
+// |F_c|_1, then H += D in FP64 and the FP64 fluid R becomes R + d P D - D
+// (Eq. HnFn, computed in FP64 by a pull over the in-links of every node:
+// deterministic, no atomics except for rows split across warps).  By
+// linearity that is the exact residual (1-d) Z + d P H - H of the new H
+// whatever the rounding of D, so the stop test, applied to the FP64 |R_c|_1,
+// is certified in FP64; D's rounding only leaves the next cycle a slightly
+// larger residual (about 6e-8 of the fluid taken, like the FP32 fluid itself).
 //
-// One sweep: k_bsel (per-column partials, frontier mask) -> k_btot (per-column
-// totals, thresholds, stop tests) -> k_btake (take the selected rows into V)
-// -> k_bpush (scatter V rows along the links; rows longer than BHUB are cut
-// into static pieces).  The sweep loop is one CUDA graph with a device-side
-// while condition, launched once per cycle.
+// One sweep: k_bsel (per-column partials of the fluid, frontier mask, and the
+// take of the selected rows: F_i -> V_i = (d/W_i) F_i, D_i += F_i, F_i = 0) ->
+// k_btot (per-column totals, thresholds, stop tests) -> k_bpush (scatter the V
+// rows along the links; rows longer than BHUB are cut into static pieces).  A
+// sweep whose totals end the cycle does not push what its selection took; that
+// fluid is in D, and the refinement's d P D pushes it exactly.  The sweep loop
+// is one CUDA graph with a device-side while condition, launched per cycle.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <string.h>
@@ -34,12 +39,14 @@ namespace di {
 using Off = uint32_t;
 constexpr int BW = 64;            // columns per node (fixed; fewer are zero-padded)
 constexpr int BT = 256;           // threads per CTA
-constexpr int BTILE = 256;        // nodes per selection tile (8 warps x 32 nodes)
+constexpr int BWARP_NODES = 128; // nodes per selection warp
+constexpr int BTILE = 1024;       // nodes per selection tile (8 warps x 128 nodes)
 constexpr Off BHUB = 256;         // longer rows are pushed as static pieces
 constexpr Off BPIECE = 256;       // links per piece
 constexpr Off PULL_CH = 512;      // in-links per refinement chunk
 constexpr unsigned FULLM = 0xffffffffu;
 constexpr int BMAX_CYCLES = 64;
+constexpr int UNR = 4;            // link pairs in flight per push iteration
 
 struct BCtl {
     float theta[BW];              // per-column threshold (FP32, rounded up); +inf when inactive
@@ -53,6 +60,7 @@ struct BCtl {
     unsigned long long pending;   // columns whose refined |R_c|_1 is still above stop
     unsigned long long live;      // the caller's columns (bit c set for c < B)
     unsigned long long sweep, max_sweeps, edge_pushes, diffusions, sweep_links;
+    unsigned col_on[BW];          // per-column decision of the last totals
     unsigned done;                // 0 running, 1 cycle over, 2 sweep cap
     unsigned push_ready;
     unsigned ticket;
@@ -126,7 +134,7 @@ __global__ void k_bdscale(const Off *rp, const double *wsum, int64_t n, double d
 
 // R = (1 - d) Z (zero-padded to BW columns), H = D = 0.
 __global__ void k_binit(const double *Z, int B, int64_t n, int64_t slots, double one_minus_d, double zu, double *R,
-                        double *H, double *D)
+                        double *H, float *D)
 {
     const int64_t total = slots * BW;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
@@ -136,16 +144,19 @@ __global__ void k_binit(const double *Z, int B, int64_t n, int64_t slots, double
         if (i < n && c < B) z = Z ? Z[i * B + c] : zu;
         R[k] = one_minus_d * z;
         H[k] = 0.0;
-        D[k] = 0.0;
+        D[k] = 0.0f;
     }
 }
 
 // ------------------------------------------------------------------ sweep
 // Half-warp h of a warp handles node base + 2 it + h; lane q = lane & 15 owns
-// columns 4q .. 4q + 3.
-__global__ void __launch_bounds__(BT) k_bsel(const float *F, int64_t n, unsigned *mask, float *tl1, unsigned *tmax,
-                                            unsigned *tcnt, BCtl *ctl, int use_cond, cudaGraphConditionalHandle cond)
+// columns 4q .. 4q + 3.  A warp covers BWARP_NODES nodes (4 mask words).
+__global__ void __launch_bounds__(BT) k_bsel(float *F, int64_t n, float *__restrict__ D, float *__restrict__ V,
+                                            const float *__restrict__ dscale, unsigned *mask, float *tl1,
+                                            unsigned *tmax, unsigned *tcnt, BCtl *ctl, int use_cond,
+                                            cudaGraphConditionalHandle cond)
 {
+    constexpr int NWORD = BWARP_NODES / 32;
     __shared__ float s_l1[BT / 32][BW];
     __shared__ unsigned s_mx[BT / 32][BW];
     __shared__ unsigned s_cnt[BT / 32];
@@ -158,30 +169,51 @@ __global__ void __launch_bounds__(BT) k_bsel(const float *F, int64_t n, unsigned
         return;
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, half = lane >> 4, q = lane & 15;
-    const int64_t base = ((int64_t)blockIdx.x * (BT / 32) + warp) * 32;
+    const int64_t base = ((int64_t)blockIdx.x * (BT / 32) + warp) * BWARP_NODES;
     float th[4];
 #pragma unroll
     for (int k = 0; k < 4; k++) th[k] = vc->theta[4 * q + k];
     float a[4] = {0.f, 0.f, 0.f, 0.f};
     unsigned m[4] = {0u, 0u, 0u, 0u};
-    unsigned word = 0;
-#pragma unroll 4
-    for (int it = 0; it < 16; it++) {
-        const int64_t i = base + 2 * it + half;
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (i < n) v = __ldcg(reinterpret_cast<const float4 *>(F + i * BW + 4 * q));
-        const float x[4] = {fabsf(v.x), fabsf(v.y), fabsf(v.z), fabsf(v.w)};
-        bool s = false;
+    unsigned words[NWORD];
+    unsigned cnt = 0;
 #pragma unroll
-        for (int k = 0; k < 4; k++) {
-            a[k] = __fadd_ru(a[k], x[k]);
-            const unsigned xb = __float_as_uint(x[k]);
-            m[k] = xb > m[k] ? xb : m[k];
-            s |= (x[k] != 0.0f) && (x[k] >= th[k]);
+    for (int wd = 0; wd < NWORD; wd++) {
+        unsigned word = 0;
+#pragma unroll
+        for (int it = 0; it < 16; it++) {
+            const int64_t i = base + 32 * wd + 2 * it + half;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (i < n) v = __ldcg(reinterpret_cast<const float4 *>(F + i * BW + 4 * q));
+            const float x[4] = {fabsf(v.x), fabsf(v.y), fabsf(v.z), fabsf(v.w)};
+            bool s = false;
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                a[k] = __fadd_ru(a[k], x[k]);
+                const unsigned xb = __float_as_uint(x[k]);
+                m[k] = xb > m[k] ? xb : m[k];
+                s |= (x[k] != 0.0f) && (x[k] >= th[k]);
+            }
+            const unsigned b = __ballot_sync(FULLM, s);
+            word |= (unsigned)((b & 0xffffu) != 0u) << (2 * it);
+            word |= (unsigned)((b >> 16) != 0u) << (2 * it + 1);
+            // take the selected node now (its row is in registers): the partials
+            // above are those of the fluid before the take
+            if ((half ? (b >> 16) : (b & 0xffffu)) != 0u) {
+                *reinterpret_cast<float4 *>(F + i * BW + 4 * q) = make_float4(0.f, 0.f, 0.f, 0.f);
+                float4 *dp = reinterpret_cast<float4 *>(D + i * BW + 4 * q);
+                float4 dd = *dp;
+                dd.x += v.x;
+                dd.y += v.y;
+                dd.z += v.z;
+                dd.w += v.w;
+                *dp = dd;
+                const float sc = __ldg(dscale + i);
+                *reinterpret_cast<float4 *>(V + i * BW + 4 * q) = make_float4(v.x * sc, v.y * sc, v.z * sc, v.w * sc);
+            }
         }
-        const unsigned b = __ballot_sync(FULLM, s);
-        word |= (unsigned)((b & 0xffffu) != 0u) << (2 * it);
-        word |= (unsigned)((b >> 16) != 0u) << (2 * it + 1);
+        words[wd] = word;
+        cnt += __popc(word);
     }
 #pragma unroll
     for (int k = 0; k < 4; k++) {
@@ -196,10 +228,14 @@ __global__ void __launch_bounds__(BT) k_bsel(const float *F, int64_t n, unsigned
             s_mx[warp][4 * q + k] = m[k];
         }
     }
-    if (lane == 0) {
-        mask[base / 32] = word;
-        s_cnt[warp] = __popc(word);
+    if (lane < NWORD) {
+        unsigned wv = words[0];
+#pragma unroll
+        for (int wd = 1; wd < NWORD; wd++)
+            if (lane == wd) wv = words[wd];
+        mask[base / 32 + lane] = wv;
     }
+    if (lane == 0) s_cnt[warp] = cnt;
     __syncthreads();
     if (threadIdx.x < BW) {
         const int c = threadIdx.x;
@@ -222,47 +258,69 @@ __global__ void __launch_bounds__(BT) k_bsel(const float *F, int64_t n, unsigned
 }
 
 // Per-column totals in a fixed order (every partial rounded up: an upper
-// bound of |F_c|_1), the per-column end of the cycle, the next thresholds.
-__global__ void __launch_bounds__(1024) k_btot(const float *tl1, const unsigned *tmax, const unsigned *tcnt,
-                                              int64_t ntiles, int64_t n, BCtl *ctl, int use_cond,
-                                              cudaGraphConditionalHandle cond)
+// bound of |F_c|_1): CTA c sums column c, decides whether the column has
+// reached the end of its cycle and sets its next threshold; the last CTA to
+// finish assembles the active set and the loop decision.
+__global__ void __launch_bounds__(BT) k_btot(const float *tl1, const unsigned *tmax, const unsigned *tcnt,
+                                            int64_t ntiles, int64_t n, BCtl *ctl, int use_cond,
+                                            cudaGraphConditionalHandle cond)
 {
-    __shared__ float s_l1[16][BW];
-    __shared__ unsigned s_mx[16][BW];
-    __shared__ unsigned long long s_c[32];
+    __shared__ float s_l1[BT / 32];
+    __shared__ unsigned s_mx[BT / 32];
+    __shared__ unsigned long long s_c[BT / 32];
+    __shared__ int s_last;
     volatile BCtl *vc = ctl;
     if (vc->done) return;
-    const int c = threadIdx.x & (BW - 1), g = threadIdx.x >> 6;
+    const int c = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float t = 0.0f;
     unsigned mx = 0;
-    for (int64_t k = g; k < ntiles; k += 16) {
+    for (int64_t k = threadIdx.x; k < ntiles; k += BT) {
         t = __fadd_ru(t, tl1[k * BW + c]);
         const unsigned y = tmax[k * BW + c];
         mx = y > mx ? y : mx;
     }
-    s_l1[g][c] = t;
-    s_mx[g][c] = mx;
-    unsigned long long cnt = 0;
-    for (int64_t k = threadIdx.x; k < ntiles; k += 1024) cnt += tcnt[k];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(FULLM, cnt, o);
-    if ((threadIdx.x & 31) == 0) s_c[threadIdx.x >> 5] = cnt;
-    __syncthreads();
-    if (threadIdx.x < BW) {
-        float tt = s_l1[0][c];
-        unsigned m2 = s_mx[0][c];
-        for (int gg = 1; gg < 16; gg++) {
-            tt = __fadd_ru(tt, s_l1[gg][c]);
-            m2 = s_mx[gg][c] > m2 ? s_mx[gg][c] : m2;
-        }
-        s_l1[0][c] = tt;
-        s_mx[0][c] = m2;
+    for (int o = 16; o > 0; o >>= 1) {
+        t = __fadd_ru(t, __shfl_xor_sync(FULLM, t, o));
+        const unsigned y = __shfl_xor_sync(FULLM, mx, o);
+        mx = y > mx ? y : mx;
+    }
+    if (lane == 0) {
+        s_l1[warp] = t;
+        s_mx[warp] = mx;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        unsigned long long act = vc->act;
+        float tt = s_l1[0];
+        unsigned m2 = s_mx[0];
+        for (int w = 1; w < BT / 32; w++) {
+            tt = __fadd_ru(tt, s_l1[w]);
+            m2 = s_mx[w] > m2 ? s_mx[w] : m2;
+        }
+        const bool was_on = (vc->act >> c) & 1ull;
+        const bool on = was_on && !((double)tt <= vc->sweep_stop[c]);
+        float th = __double2float_ru(vc->theta_factor * (double)tt / (double)n);
+        const float mxf = __uint_as_float(m2);
+        if (th > mxf) th = mxf;   // the largest fluid passes the exact test
+        vc->theta[c] = on ? th : __int_as_float(0x7f800000);
+        vc->l1f[c] = tt;
+        vc->col_on[c] = on ? 1u : 0u;
+        __threadfence();
+        s_last = atomicAdd((unsigned *)&ctl->ticket, 1u) == BW - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    unsigned long long cnt = 0;
+    for (int64_t k = threadIdx.x; k < ntiles; k += BT) cnt += tcnt[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(FULLM, cnt, o);
+    if (lane == 0) s_c[warp] = cnt;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long act = 0;
         for (int k = 0; k < BW; k++)
-            if (((act >> k) & 1ull) && (double)s_l1[0][k] <= vc->sweep_stop[k]) act &= ~(1ull << k);
+            if (vc->col_on[k]) act |= 1ull << k;
         const unsigned long long sweep = vc->sweep;
         vc->edge_pushes = vc->edge_pushes + vc->sweep_links;
         vc->sweep_links = 0;
@@ -270,54 +328,14 @@ __global__ void __launch_bounds__(1024) k_btot(const float *tl1, const unsigned 
         vc->act = act;
         if (!done) {
             unsigned long long nsel = 0;
-            for (int w = 0; w < 32; w++) nsel += s_c[w];
+            for (int w = 0; w < BT / 32; w++) nsel += s_c[w];
             vc->diffusions = vc->diffusions + nsel;
         }
+        vc->ticket = 0;
         vc->push_ready = done ? 0u : 1u;
         __threadfence();
         vc->done = done;
         if (use_cond) cudaGraphSetConditional(cond, done ? 0u : 1u);
-    }
-    __syncthreads();
-    if (threadIdx.x < BW) {
-        const bool on = (vc->act >> c) & 1ull;
-        float th = __double2float_ru(vc->theta_factor * (double)s_l1[0][c] / (double)n);
-        const float mxf = __uint_as_float(s_mx[0][c]);
-        if (th > mxf) th = mxf;   // the largest fluid passes the exact test
-        vc->theta[c] = on ? th : __int_as_float(0x7f800000);
-        vc->l1f[c] = s_l1[0][c];
-    }
-}
-
-// Take the selected rows: V_i = (d / W_i) F_i (FP32), D_i += F_i (exact, FP64),
-// F_i = 0.  One warp per mask word; half-warp per node.
-__global__ void __launch_bounds__(BT) k_btake(float *F, double *D, float *V, const float *dscale,
-                                             const unsigned *mask, int64_t words, const BCtl *ctl)
-{
-    const volatile BCtl *vc = ctl;
-    if (!vc->push_ready) return;
-    const int lane = threadIdx.x & 31, half = lane >> 4, q = lane & 15;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t wi = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; wi < words; wi += nw) {
-        const unsigned word = mask[wi];
-        const int cnt = __popc(word);
-        for (int r = half; r < cnt; r += 2) {
-            const int p = __fns(word, 0, r + 1);   // position of the (r+1)-th set bit
-            const int64_t i = wi * 32 + p;
-            float4 *fp = reinterpret_cast<float4 *>(F + i * BW + 4 * q);
-            const float4 f = *fp;
-            *fp = make_float4(0.f, 0.f, 0.f, 0.f);
-            double2 *dp = reinterpret_cast<double2 *>(D + i * BW + 4 * q);
-            double2 d0 = dp[0], d1 = dp[1];
-            d0.x += (double)f.x;
-            d0.y += (double)f.y;
-            d1.x += (double)f.z;
-            d1.y += (double)f.w;
-            dp[0] = d0;
-            dp[1] = d1;
-            const float s = dscale[i];
-            *reinterpret_cast<float4 *>(V + i * BW + 4 * q) = make_float4(f.x * s, f.y * s, f.z * s, f.w * s);
-        }
     }
 }
 
@@ -357,28 +375,40 @@ __global__ void __launch_bounds__(BT) k_bpush(float *F, const float *V, const Of
             const Off total = __shfl_sync(FULLM, incl, 31);
             const Off excl = incl - deg;
             links += total;
-            for (Off e = 0; e < total; e += 2) {
-                const Off ee = e + half < total ? e + half : total - 1;
-                int j = 0;
+            // 4 link pairs in flight per iteration: all loads first, then the adds
+            for (Off e = 0; e < total; e += 2 * UNR) {
+                Off link[UNR];
+                int64_t src[UNR];
 #pragma unroll
-                for (int step = 16; step > 0; step >>= 1) {
-                    const Off ex = __shfl_sync(FULLM, excl, j + step);
-                    if (ex <= ee) j += step;
-                }
-                const Off link = __shfl_sync(FULLM, r0, j) + (ee - __shfl_sync(FULLM, excl, j));
-                if (e + half < total) {
-                    const int64_t src = u * 32 + j;
-                    const int32_t c = __ldg(col + link);
-                    float4 v = __ldg(reinterpret_cast<const float4 *>(V + src * BW + 4 * q));
-                    if (w32) {
-                        const float wl = __ldg(w32 + link);
-                        v.x *= wl;
-                        v.y *= wl;
-                        v.z *= wl;
-                        v.w *= wl;
+                for (int k = 0; k < UNR; k++) {
+                    const Off ee0 = e + 2 * k + half;
+                    const Off ee = ee0 < total ? ee0 : total - 1;
+                    int j = 0;
+#pragma unroll
+                    for (int step = 16; step > 0; step >>= 1) {
+                        const Off ex = __shfl_sync(FULLM, excl, j + step);
+                        if (ex <= ee) j += step;
                     }
-                    red_v4(F + (int64_t)c * BW + 4 * q, v);
+                    link[k] = __shfl_sync(FULLM, r0, j) + (ee - __shfl_sync(FULLM, excl, j));
+                    src[k] = u * 32 + j;
                 }
+                int32_t c[UNR];
+                float4 v[UNR];
+#pragma unroll
+                for (int k = 0; k < UNR; k++) {
+                    c[k] = __ldg(col + link[k]);
+                    v[k] = __ldg(reinterpret_cast<const float4 *>(V + src[k] * BW + 4 * q));
+                    if (w32) {
+                        const float wl = __ldg(w32 + link[k]);
+                        v[k].x *= wl;
+                        v[k].y *= wl;
+                        v[k].z *= wl;
+                        v[k].w *= wl;
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < UNR; k++)
+                    if (e + 2 * k + half < total) red_v4(F + (int64_t)c[k] * BW + 4 * q, v[k]);
             }
         } else {
             const int64_t p = u - words;
@@ -387,18 +417,25 @@ __global__ void __launch_bounds__(BT) k_bpush(float *F, const float *V, const Of
             const Off s0 = pc_start[p], len = pc_len[p];
             links += len;
             const float4 v0 = __ldg(reinterpret_cast<const float4 *>(V + (int64_t)row * BW + 4 * q));
-            for (Off e = half; e < len; e += 2) {
-                const Off link = s0 + e;
-                const int32_t c = __ldg(col + link);
-                float4 v = v0;
-                if (w32) {
-                    const float wl = __ldg(w32 + link);
-                    v.x *= wl;
-                    v.y *= wl;
-                    v.z *= wl;
-                    v.w *= wl;
+            for (Off e = half; e < len; e += 2 * UNR) {
+                int32_t c[UNR];
+                float4 v[UNR];
+#pragma unroll
+                for (int k = 0; k < UNR; k++) {
+                    const Off link = s0 + (e + 2 * k < len ? e + 2 * k : len - 1);
+                    c[k] = __ldg(col + link);
+                    v[k] = v0;
+                    if (w32) {
+                        const float wl = __ldg(w32 + link);
+                        v[k].x *= wl;
+                        v[k].y *= wl;
+                        v[k].z *= wl;
+                        v[k].w *= wl;
+                    }
                 }
-                red_v4(F + (int64_t)c * BW + 4 * q, v);
+#pragma unroll
+                for (int k = 0; k < UNR; k++)
+                    if (e + 2 * k < len) red_v4(F + (int64_t)c[k] * BW + 4 * q, v[k]);
             }
         }
     }
@@ -456,24 +493,36 @@ __global__ void __launch_bounds__(BT) k_bpull(const Off *rrp, const int32_t *rco
     }
 }
 
+// D64 = D: the FP64 copy the pull reads (one conversion per value instead of
+// one per link and value; FP64 work is scarce on this part).
+__global__ void k_bwiden(const float *D, int64_t total, double *D64)
+{
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < total / 4;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const float4 v = reinterpret_cast<const float4 *>(D)[k];
+        reinterpret_cast<double2 *>(D64)[2 * k] = make_double2((double)v.x, (double)v.y);
+        reinterpret_cast<double2 *>(D64)[2 * k + 1] = make_double2((double)v.z, (double)v.w);
+    }
+}
+
 // F = fl(R) (FP32), D = 0, per-column exact |R_c|_1 partials (FP64, fixed
 // order) and max |F_c| per tile of BTILE nodes.
-__global__ void __launch_bounds__(BT) k_bconv(const double *R, float *F, double *D, int64_t slots, double *tl1d,
+__global__ void __launch_bounds__(BT) k_bconv(const double *R, float *F, float *D, int64_t slots, double *tl1d,
                                              unsigned *tmax)
 {
     __shared__ double s_a[BT / 32][BW];
     __shared__ unsigned s_m[BT / 32][BW];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t base = ((int64_t)blockIdx.x * (BT / 32) + warp) * 32;
+    const int64_t base = ((int64_t)blockIdx.x * (BT / 32) + warp) * BWARP_NODES;
     double a0 = 0.0, a1 = 0.0;
     unsigned m0 = 0, m1 = 0;
-    for (int it = 0; it < 32; it++) {
+    for (int it = 0; it < BWARP_NODES; it++) {
         const int64_t i = base + it;
         if (i >= slots) break;
         const double2 r = reinterpret_cast<const double2 *>(R + i * BW)[lane];
         const float2 f = make_float2((float)r.x, (float)r.y);
         reinterpret_cast<float2 *>(F + i * BW)[lane] = f;
-        reinterpret_cast<double2 *>(D + i * BW)[lane] = make_double2(0.0, 0.0);
+        reinterpret_cast<float2 *>(D + i * BW)[lane] = make_float2(0.0f, 0.0f);
         a0 += fabs(r.x);
         a1 += fabs(r.y);
         const unsigned b0 = __float_as_uint(fabsf(f.x)), b1 = __float_as_uint(fabsf(f.y));
@@ -562,8 +611,8 @@ __global__ void k_bgather(const double *H, int64_t n, int B, double *out)
 // ------------------------------------------------------------------- host
 struct BatchBufs {
     int64_t n = 0, slots = 0, ntiles = 0, words = 0, npieces = 0, nch = 0;
-    float *F = nullptr, *V = nullptr, *dscale = nullptr;
-    double *D = nullptr, *H = nullptr, *R = nullptr;
+    float *F = nullptr, *V = nullptr, *dscale = nullptr, *D = nullptr;
+    double *H = nullptr, *R = nullptr, *D64 = nullptr;
     unsigned *mask = nullptr, *hubbits = nullptr, *tmax = nullptr, *tcnt = nullptr;
     float *tl1 = nullptr;
     double *tl1d = nullptr;
@@ -575,22 +624,23 @@ struct BatchBufs {
 static void launch_sweep(di_graph_s *g, BatchBufs &b, cudaStream_t s, int use_cond, cudaGraphConditionalHandle h,
                          int grid)
 {
-    k_bsel<<<(unsigned)b.ntiles, BT, 0, s>>>(b.F, b.n, b.mask, b.tl1, b.tmax, b.tcnt, b.ctl, use_cond, h);
-    k_btot<<<1, 1024, 0, s>>>(b.tl1, b.tmax, b.tcnt, b.ntiles, b.n, b.ctl, use_cond, h);
-    k_btake<<<grid, BT, 0, s>>>(b.F, b.D, b.V, b.dscale, b.mask, b.words, b.ctl);
+    k_bsel<<<(unsigned)b.ntiles, BT, 0, s>>>(b.F, b.n, b.D, b.V, b.dscale, b.mask, b.tl1, b.tmax, b.tcnt, b.ctl,
+                                             use_cond, h);
+    k_btot<<<BW, BT, 0, s>>>(b.tl1, b.tmax, b.tcnt, b.ntiles, b.n, b.ctl, use_cond, h);
     k_bpush<<<grid, BT, 0, s>>>(b.F, b.V, static_cast<const Off *>(g->rp), g->col, g->weighted ? g->w32 : nullptr,
                                 b.mask, b.hubbits, b.words, b.pc_row, b.pc_start, b.pc_len, b.npieces, b.ctl);
-    count_launches(4);
+    count_launches(3);
 }
 
 static di_status refine(di_graph_s *g, BatchBufs &b, double d, cudaStream_t s)
 {
     di_graph_s *r = g->rev;
+    k_bwiden<<<grid_for(b.slots * BW / 4, BT), BT, 0, s>>>(b.D, b.slots * BW, b.D64);
     k_bpull<<<grid_for(b.nch * 32, BT), BT, 0, s>>>(static_cast<const Off *>(r->rp), r->col, r->w, b.ch_row,
-                                                    b.ch_start, b.ch_len, b.nch, d, b.D, b.R, b.H);
+                                                    b.ch_start, b.ch_len, b.nch, d, b.D64, b.R, b.H);
     k_bconv<<<(unsigned)b.ntiles, BT, 0, s>>>(b.R, b.F, b.D, b.slots, b.tl1d, b.tmax);
     k_bcycle<<<1, 1024, 0, s>>>(b.tl1d, b.tmax, b.ntiles, b.n, b.ctl);
-    count_launches(3);
+    count_launches(4);
     DI_CUDA(cudaGetLastError());
     return DI_OK;
 }
@@ -612,6 +662,7 @@ di_status solve_batch(di_graph_s *g, int B, double d, const double *Z, double to
     DI_TRY(t.get(&b.D, b.slots * BW));
     DI_TRY(t.get(&b.H, b.slots * BW));
     DI_TRY(t.get(&b.R, b.slots * BW));
+    DI_TRY(t.get(&b.D64, b.slots * BW));
     DI_TRY(t.get(&b.dscale, n));
     DI_TRY(t.get(&b.mask, b.words));
     DI_TRY(t.get(&b.hubbits, b.words));
@@ -739,7 +790,7 @@ di_status solve_batch(di_graph_s *g, int B, double d, const double *Z, double to
     if (gx) cudaGraphExecDestroy(gx);
     if (cs) cudaStreamDestroy(cs);
     if (rc != DI_OK) return rc;
-    if (graph_mode) count_launches(4 * (int64_t)(hc.sweep + refinements));
+    if (graph_mode) count_launches(3 * (int64_t)(hc.sweep + refinements));
     if (H_out) {
         double *dst = H_out;
         if (mem == DI_MEM_HOST) DI_TRY(t.get(&dst, n * B));
