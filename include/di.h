@@ -221,7 +221,8 @@ di_status di_state_import(di_state_t s, const double *H, const double *F, double
  *            column uniform 1/n
  *   tol      > 0, for every column
  *   opts     NULL = defaults; theta_factor, max_sweeps, use_graph, check_every and
- *            refine_ratio apply; precision and profile are ignored
+ *            refine_ratio apply; precision is ignored; profile = 1 runs the loop
+ *            one sweep at a time and fills push_ms / push_launches / push_edges
  *   H_out    float64[n][B] in `mem` (node-major) or NULL
  *   resid_out float64[B] in `mem` or NULL: |F_c|_1 of each column's returned
  *            state (exact FP64 sum in a fixed order)

@@ -622,13 +622,15 @@ struct BatchBufs {
 };
 
 static void launch_sweep(di_graph_s *g, BatchBufs &b, cudaStream_t s, int use_cond, cudaGraphConditionalHandle h,
-                         int grid)
+                         int grid, cudaEvent_t ev_a = nullptr, cudaEvent_t ev_b = nullptr)
 {
     k_bsel<<<(unsigned)b.ntiles, BT, 0, s>>>(b.F, b.n, b.D, b.V, b.dscale, b.mask, b.tl1, b.tmax, b.tcnt, b.ctl,
                                              use_cond, h);
     k_btot<<<BW, BT, 0, s>>>(b.tl1, b.tmax, b.tcnt, b.ntiles, b.n, b.ctl, use_cond, h);
+    if (ev_a) cudaEventRecord(ev_a, s);
     k_bpush<<<grid, BT, 0, s>>>(b.F, b.V, static_cast<const Off *>(g->rp), g->col, g->weighted ? g->w32 : nullptr,
                                 b.mask, b.hubbits, b.words, b.pc_row, b.pc_start, b.pc_len, b.npieces, b.ctl);
+    if (ev_b) cudaEventRecord(ev_b, s);
     count_launches(3);
 }
 
@@ -752,9 +754,15 @@ di_status solve_batch(di_graph_s *g, int B, double d, const double *Z, double to
             return note_cuda(e);
         }
     }
-    cudaEvent_t e0, e1;
+    cudaEvent_t e0, e1, pa = nullptr, pb = nullptr;
     DI_CUDA(cudaEventCreate(&e0));
     DI_CUDA(cudaEventCreate(&e1));
+    if (o->profile) {
+        DI_CUDA(cudaEventCreate(&pa));
+        DI_CUDA(cudaEventCreate(&pb));
+    }
+    double push_ms = 0.0;
+    int64_t push_launches = 0, push_links = 0;
     DI_CUDA(cudaEventRecord(e0, s));
     DI_CUDA(cudaMemcpyAsync(&hc, b.ctl, sizeof(hc), cudaMemcpyDeviceToHost, s));
     DI_CUDA(cudaStreamSynchronize(s));
@@ -773,8 +781,25 @@ di_status solve_batch(di_graph_s *g, int B, double d, const double *Z, double to
             }
         } else {
             for (;;) {
-                for (int k = 0; k < o->check_every; k++)
-                    launch_sweep(g, b, s, 0, cudaGraphConditionalHandle{}, grid);
+                for (int k = 0; k < o->check_every; k++) {
+                    if (o->profile) {
+                        // one sweep at a time: time its push, and take its links
+                        // from the totals of the next sweep
+                        launch_sweep(g, b, s, 0, cudaGraphConditionalHandle{}, grid, pa, pb);
+                        DI_CUDA(cudaMemcpyAsync(&hc, b.ctl, sizeof(hc), cudaMemcpyDeviceToHost, s));
+                        DI_CUDA(cudaStreamSynchronize(s));
+                        if (hc.push_ready) {
+                            float pm = 0.f;
+                            DI_CUDA(cudaEventElapsedTime(&pm, pa, pb));
+                            push_ms += pm;
+                            push_launches++;
+                            push_links += (int64_t)hc.sweep_links;
+                        }
+                        if (hc.done) break;
+                    } else {
+                        launch_sweep(g, b, s, 0, cudaGraphConditionalHandle{}, grid);
+                    }
+                }
                 DI_CUDA(cudaMemcpyAsync(&hc, b.ctl, sizeof(hc), cudaMemcpyDeviceToHost, s));
                 DI_CUDA(cudaStreamSynchronize(s));
                 if (hc.done) break;
@@ -804,6 +829,8 @@ di_status solve_batch(di_graph_s *g, int B, double d, const double *Z, double to
     DI_CUDA(cudaEventElapsedTime(&ms, e0, e1));
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    if (pa) cudaEventDestroy(pa);
+    if (pb) cudaEventDestroy(pb);
     if (resid_out) {
         if (mem == DI_MEM_HOST) {
             for (int c = 0; c < B; c++) resid_out[c] = hc.l1[c];
@@ -823,6 +850,9 @@ di_status solve_batch(di_graph_s *g, int B, double d, const double *Z, double to
         info->edge_pushes = (int64_t)hc.edge_pushes;
         info->time_ms = ms;
         info->refinements = refinements;
+        info->push_ms = push_ms;
+        info->push_launches = push_launches;
+        info->push_edges = push_links;
     }
     if (hc.done == 2) return DI_ERR_NOT_CONVERGED;
     return DI_OK;

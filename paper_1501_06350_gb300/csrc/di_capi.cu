@@ -342,7 +342,6 @@ di_status di_solve_batch(di_graph_t g, int32_t B, double d, const double *Z, dou
     di_opts_default(&o);
     if (opts) o = *opts;
     o.precision = DI_PREC_F32;
-    o.profile = 0;
     DI_TRY(opts_ok(&o));
     DeviceScope ds(g->device);
     cudaStream_t s = as_stream(stream);
