@@ -322,6 +322,8 @@ def main():
                     help="skip the side-by-side time to tol of both forms")
     ap.add_argument("--no-adjoint", action="store_true",
                     help="skip the backward-pass timing on the 2M-page weighted graph")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="time the step with the library defaults instead of the autotuned options")
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the batched personalised solve and the union of 256 small graphs")
     args = ap.parse_args()
@@ -358,9 +360,20 @@ def main():
     L = _lib.lib()
 
     ug = 0 if args.eager else 1
-    sopt = {} if args.theta is None else {"theta_factor": args.theta}
+    sopt = {}
+    tuning = None
     if args.precision == "f32":
         sopt["precision"] = _lib.DI_PREC_F32
+    if not args.no_tune:
+        # one-time tuning of the launch shape on this graph (outside the timed region)
+        tuned, trep = di.autotune(G, D, TOL, sopt.get("precision", 0), 20)
+        sopt.update({k: tuned[k] for k in ("theta_factor", "hub_deg", "piece")})
+        if args.precision == "f32":
+            sopt["refine_ratio"] = tuned["refine_ratio"]
+        tuning = {"options": {k: sopt[k] for k in sopt}, "tuned_ms": trep["best_ms"],
+                  "default_ms": trep["default_ms"], "trials": trep["trials"]}
+    if args.theta is not None:
+        sopt["theta_factor"] = args.theta
 
     def step():
         H, i1 = st.solve(D, tol=TOL, use_graph=ug, **sopt)
@@ -449,7 +462,7 @@ def main():
            "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None,
            "dtype": "f32 fluid / f64 history" if args.precision == "f32" else "f64", "data": "synthetic",
-           "config": config_dict(g, gi, args.precision),
+           "config": dict(config_dict(g, gi, args.precision), tuning=tuning),
            "time_to_tol_ms": statistics.median(solve_ms),
            "solve": {"edge_pushes": solve_pushes, "sweeps": statistics.median([i1["sweeps"] for i1, _, _ in infos]),
                      "edge_pushes_per_s": solve_pushes / (statistics.median(solve_ms) / 1e3),

@@ -79,6 +79,12 @@ typedef struct {
                               is applied to that FP64 residual only, so the returned
                               bound is certified in FP64 whatever the FP32 rounding. */
     double refine_ratio;   /* DI_PREC_F32 only: 0 < refine_ratio < 1.               */
+    int32_t hub_deg;       /* degree-bin threshold: rows with more links than this are
+                              taken by the plan kernel and pushed as pieces by many
+                              warps; shorter rows are pushed by the warp that owns
+                              their 128-node unit.  32 <= hub_deg <= 65536.            */
+    int32_t piece;         /* links per hub piece (tile of the hub push), 128 <= piece
+                              <= 65536.                                               */
 } di_opts;
 
 /* Solver report. */
@@ -102,7 +108,8 @@ typedef struct {
 } di_info;
 
 /* Fill *o with the defaults: theta_factor 1, max_sweeps 100000, check_every 8,
-   use_graph 1, normalize 0, profile 0, precision DI_PREC_F64, refine_ratio 1e-5. */
+   use_graph 1, normalize 0, profile 0, precision DI_PREC_F64, refine_ratio 1e-5,
+   hub_deg 256, piece 1024. */
 void di_opts_default(di_opts *o);
 
 /* Human-readable name of a status code (static storage). */
@@ -200,6 +207,24 @@ di_status di_state_export(di_state_t s, double *H, double *F, double *l, int mem
  * damping d for later di_resume calls.  Both float64[n], finite. */
 di_status di_state_import(di_state_t s, const double *H, const double *F, double d, int mem,
                           void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Autotuner (not in the paper).  Times from-scratch solves of g (uniform
+ * teleport vector, damping d, tolerance tol, fluid precision `precision`) and
+ * returns in *out the options that were fastest: one pass of coordinate search
+ * over the threshold factor c (Section 3.4), the degree-bin threshold hub_deg,
+ * the hub piece size and (DI_PREC_F32) the refinement ratio, starting from
+ * di_opts_default; each candidate is the best of two solves (device time).
+ *   budget      maximum number of candidates timed (>= 1; 20 covers the pass)
+ *   cache_path  NULL, or a text file: a line for this graph shape, d, tol and
+ *               precision is reused without timing anything; a new result is
+ *               appended (one line per tuned problem).
+ *   out         receives di_opts_default with the tuned fields
+ *   best_ms, default_ms   time of the tuned and of the default options (may be NULL)
+ *   trials      candidates timed by this call (0 when taken from the cache; may be NULL)
+ * The graph itself is not changed; a private solver state is used. */
+di_status di_autotune(di_graph_t g, double d, double tol, int32_t precision, int32_t budget, const char *cache_path,
+                      di_opts *out, double *best_ms, double *default_ms, int32_t *trials, void *stream);
 
 /* ---------------------------------------------------------------------------
  * Batched personalised solves: B teleport vectors on one graph (topic-

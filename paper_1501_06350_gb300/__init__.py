@@ -8,7 +8,7 @@ first call that needs libdi.so loads it and fails loudly when it is missing.
 """
 import importlib
 
-__all__ = ["Graph", "State", "solve", "solve_batch", "frontier_select", "residual_l1", "adjoint", "PageRank",
+__all__ = ["Graph", "State", "solve", "solve_batch", "autotune", "frontier_select", "residual_l1", "adjoint", "PageRank",
            "pagerank"]
 
 

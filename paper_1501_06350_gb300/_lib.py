@@ -35,7 +35,8 @@ class di_opts(ctypes.Structure):
     _fields_ = [("theta_factor", ctypes.c_double), ("max_sweeps", ctypes.c_int64),
                 ("check_every", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("normalize", ctypes.c_int32), ("profile", ctypes.c_int32),
-                ("precision", ctypes.c_int32), ("refine_ratio", ctypes.c_double)]
+                ("precision", ctypes.c_int32), ("refine_ratio", ctypes.c_double),
+                ("hub_deg", ctypes.c_int32), ("piece", ctypes.c_int32)]
 
 
 class di_info(ctypes.Structure):
@@ -88,6 +89,9 @@ SIGNATURES = {
     "di_update_edges": (INT, [P, P, I64, P, P, P, P, INT, P]),
     "di_state_export": (INT, [P, P, P, P, INT, P]),
     "di_state_import": (INT, [P, P, P, ctypes.c_double, INT, P]),
+    "di_autotune": (INT, [P, ctypes.c_double, ctypes.c_double, ctypes.c_int32, ctypes.c_int32, ctypes.c_char_p,
+                          ctypes.POINTER(di_opts), ctypes.POINTER(ctypes.c_double),
+                          ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32), P]),
     "di_solve_batch": (INT, [P, ctypes.c_int32, ctypes.c_double, P, ctypes.c_double, ctypes.POINTER(di_opts),
                              P, P, ctypes.POINTER(di_info), INT, P]),
     "di_adjoint": (INT, [P, ctypes.c_double, P, P, ctypes.c_double, ctypes.POINTER(di_opts), P, P, P,

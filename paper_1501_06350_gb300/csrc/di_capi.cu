@@ -66,6 +66,7 @@ di_status opts_ok(const di_opts *o)
     if (o->precision != DI_PREC_F64 && o->precision != DI_PREC_F32) return DI_ERR_INVALID_ARG;
     if (o->precision == DI_PREC_F32 && !(o->refine_ratio > 0.0 && o->refine_ratio < 1.0))
         return DI_ERR_INVALID_ARG;
+    if (o->hub_deg < 32 || o->hub_deg > 65536 || o->piece < 128 || o->piece > 65536) return DI_ERR_INVALID_ARG;
     return DI_OK;
 }
 
@@ -112,6 +113,8 @@ void di_opts_default(di_opts *o)
     o->profile = 0;
     o->precision = DI_PREC_F64;
     o->refine_ratio = 1e-5;
+    o->hub_deg = 256;
+    o->piece = 1024;
 }
 
 const char *di_status_str(di_status s)
@@ -330,6 +333,23 @@ di_status di_state_import(di_state_t st, const double *H, const double *F, doubl
     st->d = d;
     st->have_problem = true;
     st->problem_version = st->g->version;
+    return DI_OK;
+}
+
+di_status di_autotune(di_graph_t g, double d, double tol, int32_t precision, int32_t budget, const char *cache_path,
+                      di_opts *out, double *best_ms, double *default_ms, int32_t *trials, void *stream)
+{
+    if (!g || !out || budget < 1) return DI_ERR_INVALID_ARG;
+    if (!(d > 0.0 && d < 1.0) || !(tol > 0.0) || !isfinite(tol)) return DI_ERR_INVALID_ARG;
+    if (precision != DI_PREC_F64 && precision != DI_PREC_F32) return DI_ERR_INVALID_ARG;
+    DeviceScope ds(g->device);
+    double b = 0.0, dm = 0.0;
+    int tr = 0, fc = 0;
+    di_status rc = autotune(g, d, tol, precision, budget, cache_path, out, &b, &dm, &tr, &fc, as_stream(stream));
+    if (rc != DI_OK) return rc;
+    if (best_ms) *best_ms = b;
+    if (default_ms) *default_ms = dm;
+    if (trials) *trials = fc ? 0 : tr;
     return DI_OK;
 }
 

@@ -168,12 +168,14 @@ struct di_state_s {
     double *dscale = nullptr;      // d / W_j (or d / out(j)) per node, 0 if dangling
     double dscale_d = -1.0;        // damping dscale was built for
     // frontier of the last selection: one bit per selected node that is not a
-    // hub; selected hubs (more than HUB_DEG links) go to hub_list
+    // hub; selected hubs (more than hub_deg links) go to hub_list
     unsigned int *mask = nullptr;      // [slots / 32]
-    unsigned int *hubbits = nullptr;   // [slots / 32] static: node has more than HUB_DEG links
+    unsigned int *hubbits = nullptr;   // [slots / 32] static: node has more than hub_deg links
+    int hub_deg = 256;                 // degree-bin threshold the hub bits were built for
+    int piece = 1024;                  // links per hub piece
     unsigned int *hub_list = nullptr;  // [nhub_cap]
     int64_t nhub_cap = 0;
-    // hub pieces (rows longer than HUB_DEG, cut into PIECE links)
+    // hub pieces (rows longer than hub_deg, cut into `piece` links)
     unsigned int *pc_row = nullptr;
     unsigned int *pc_len = nullptr;
     double *pc_val = nullptr;
@@ -204,8 +206,8 @@ constexpr int SEL_THREADS = 512;
 constexpr int SEL_PER_THREAD = 16;
 constexpr int TILE = SEL_THREADS * SEL_PER_THREAD;   // nodes per selection tile
 constexpr int PUSH_THREADS = 256;
-constexpr int HUB_DEG = 256;                         // longer rows are pushed as pieces
-constexpr int PIECE = 1024;                          // links per hub piece
+constexpr int HUB_DEG = 256;                         // default degree-bin threshold (di_opts.hub_deg)
+constexpr int PIECE = 1024;                          // default links per hub piece (di_opts.piece)
 constexpr int RED_THREADS = 256;
 constexpr int STAT_CAP = 4096;                       // sweeps with recorded statistics
 constexpr int PLAN_CTAS = 32;                        // CTAs of the per-sweep plan kernel
@@ -225,6 +227,10 @@ di_status state_l(di_graph_s *g, di_state_s *st, double *l, cudaStream_t s);
 di_status check_finite(const double *v, int64_t n, bool *ok, cudaStream_t s);
 di_status state_alloc(di_state_s *st, cudaStream_t s);
 di_status state_prepare_graph(di_graph_s *g, di_state_s *st, cudaStream_t s);
+di_status state_set_bins(di_graph_s *g, di_state_s *st, int hub_deg, int piece, cudaStream_t s);
+di_status autotune(di_graph_s *g, double d, double tol, int precision, int budget, const char *cache,
+                   di_opts *best, double *best_ms, double *default_ms, int *trials, int *from_cache,
+                   cudaStream_t s);
 di_status state_free(di_state_s *st);
 di_status solve_loop(di_graph_s *g, di_state_s *st, double tol, const di_opts *o, di_info *info,
                      cudaStream_t s, bool fresh, const double *Z_dev, bool inf_norm = false);

@@ -5,12 +5,12 @@
 //   select  (k_select)  streams F once: an exact fixed-point partial of
 //           |F_t|_1 and max |F_i| per tile, the DI-argmax test, and the
 //           frontier as a bit mask (one bit per node); selected hub rows
-//           (more than HUB_DEG links) go to a short list instead.
+//           (more than hub_deg links) go to a short list instead.
 //   plan    (k_plan)    every CTA sums the tile partials (integers, so all
 //           CTAs agree exactly), decides the stop test |F_t|_1/(1-d) <= tol
 //           (Theorem 1, Eq. SL) and the next threshold, and takes the fluid
 //           of the selected hubs (F is quiescent here), cutting their rows
-//           into pieces of PIECE links.
+//           into pieces of `piece` links.
 //   push    (k_push)    warp-centric: a warp takes 32 nodes with their mask
 //           word, takes the fluid of the set ones with an atomic exchange,
 //           moves it into H, and scatters d F_i P[k][i] along their links with
@@ -587,7 +587,7 @@ __global__ void __launch_bounds__(SEL_THREADS)
            int64_t ntiles, const unsigned *__restrict__ hub_list, Off *pc_row, Off *pc_len, double *pc_val,
            const unsigned *tile_cnt, const unsigned *tile_diff, const float *tile_l1f,
            const unsigned *tile_maxf, const unsigned *tile_maxu, DevCtl *ctl, int use_cond,
-           cudaGraphConditionalHandle cond, unsigned long long *stats)
+           cudaGraphConditionalHandle cond, unsigned long long *stats, Off piece)
 {
     typedef typename FluidWord<T>::U U;
     constexpr int NW = SEL_THREADS / 32;
@@ -698,11 +698,11 @@ __global__ void __launch_bounds__(SEL_THREADS)
         if (SUB) red_add_f64(reinterpret_cast<double *>(Fd) + i, -f, keep);
         const Off deg = r1 - r0;
         const double v = f * ds;
-        const unsigned np = (deg + PIECE - 1) / PIECE;
+        const unsigned np = (deg + piece - 1) / piece;
         unsigned long long pb = atomicAdd((unsigned long long *)&ctl->npieces, (unsigned long long)np);
-        for (Off o = 0; o < deg; o += PIECE) {
+        for (Off o = 0; o < deg; o += piece) {
             pc_row[pb] = r0 + o;
-            pc_len[pb] = deg - o < (Off)PIECE ? deg - o : (Off)PIECE;
+            pc_len[pb] = deg - o < piece ? deg - o : piece;
             pc_val[pb] = v;
             pb++;
         }
@@ -959,8 +959,8 @@ __global__ void __launch_bounds__(PUSH_THREADS)
     }
 }
 
-// Static hub bit mask: node i has more than HUB_DEG out-links.
-__global__ void k_hubbits(const Off *rp, int64_t n, int64_t words, unsigned *hubbits,
+// Static hub bit mask: node i has more than hub_deg out-links.
+__global__ void k_hubbits(const Off *rp, int64_t n, int64_t words, Off hub_deg, unsigned *hubbits,
                           unsigned long long *count)
 {
     unsigned long long c = 0;
@@ -969,7 +969,7 @@ __global__ void k_hubbits(const Off *rp, int64_t n, int64_t words, unsigned *hub
         unsigned word = 0;
         for (int b = 0; b < 32; b++) {
             const int64_t i = wi * 32 + b;
-            if (i < n && rp[i + 1] - rp[i] > (Off)HUB_DEG) word |= 1u << b;
+            if (i < n && rp[i + 1] - rp[i] > hub_deg) word |= 1u << b;
         }
         hubbits[wi] = word;
         c += __popc(word);
@@ -1016,8 +1016,8 @@ di_status state_prepare_graph(di_graph_s *g, di_state_s *st, cudaStream_t s)
     unsigned long long *cnt;
     DI_TRY(t.get(&cnt, 1));
     DI_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), s));
-    k_hubbits<<<grid_for(words, 256), 256, 0, s>>>(static_cast<const Off *>(g->rp), g->n, words, st->hubbits,
-                                                   cnt);
+    k_hubbits<<<grid_for(words, 256), 256, 0, s>>>(static_cast<const Off *>(g->rp), g->n, words,
+                                                   (Off)st->hub_deg, st->hubbits, cnt);
     count_launches(1);
     DI_CUDA(cudaGetLastError());
     unsigned long long nh = 0;
@@ -1029,7 +1029,7 @@ di_status state_prepare_graph(di_graph_s *g, di_state_s *st, cudaStream_t s)
         DI_TRY(dalloc_t(&st->hub_list, nh + 1, s));
         st->nhub_cap = (int64_t)nh + 1;
     }
-    const int64_t need = g->nnz / PIECE + (int64_t)nh + 2;
+    const int64_t need = g->nnz / st->piece + (int64_t)nh + 2;
     if (need > st->max_items) {
         dfree(st->pc_row, s);
         dfree(st->pc_len, s);
@@ -1042,6 +1042,24 @@ di_status state_prepare_graph(di_graph_s *g, di_state_s *st, cudaStream_t s)
         st->max_items = need;
     }
     return DI_OK;
+}
+
+// Apply the degree-bin threshold and piece size of a solve: the hub bits and
+// the piece queue follow them, and the captured sweep loops are rebuilt.
+di_status state_set_bins(di_graph_s *g, di_state_s *st, int hub_deg, int piece, cudaStream_t s)
+{
+    if (hub_deg == st->hub_deg && piece == st->piece) return DI_OK;
+    st->hub_deg = hub_deg;
+    st->piece = piece;
+    if (st->gexec) {
+        cudaGraphExecDestroy(st->gexec);
+        st->gexec = nullptr;
+    }
+    if (st->gexec32) {
+        cudaGraphExecDestroy(st->gexec32);
+        st->gexec32 = nullptr;
+    }
+    return state_prepare_graph(g, st, s);
 }
 
 di_status state_alloc(di_state_s *st, cudaStream_t s)
@@ -1138,7 +1156,7 @@ static void launch_plan(di_graph_s *g, di_state_s *st, const Sweep &w, cudaStrea
     unsigned long long *stats = w.kind == SW_REFINE ? nullptr : st->stats;
 #define DI_PLAN_ARGS                                                                                      \
     w.Hs, rp, st->dscale, g->n, st->ntiles, st->hub_list, st->pc_row, st->pc_len, st->pc_val, st->tile_cnt, \
-        st->tile_diff, st->tile_l1f, st->tile_maxf, st->tile_maxu, w.ctl, use_cond, h, stats
+        st->tile_diff, st->tile_l1f, st->tile_maxf, st->tile_maxu, w.ctl, use_cond, h, stats, (Off)st->piece
     if (w.kind == SW_F32)
         k_plan<float, false><<<PLAN_CTAS, SEL_THREADS, 0, s>>>(static_cast<float *>(w.Ft),
                                                                static_cast<float *>(w.Fd), DI_PLAN_ARGS);
@@ -1343,6 +1361,7 @@ di_status solve_loop(di_graph_s *g, di_state_s *st, double tol, const di_opts *o
     const double d = st->d;
     const bool f32 = o->precision == DI_PREC_F32;
     if (f32) DI_TRY(state_alloc_f32(st, s));
+    DI_TRY(state_set_bins(g, st, o->hub_deg, o->piece, s));
     if (fresh) {
         k_init<<<grid_for(n, 256), 256, 0, s>>>(st->F, st->H, Z_dev, n, 1.0 - d, 1.0 / (double)n);
         count_launches(1);

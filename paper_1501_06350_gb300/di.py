@@ -321,3 +321,17 @@ def solve_batch(graph: Graph, Z, d: float = 0.85, tol: float = 1e-9, device: boo
     out = info.as_dict()
     out["converged"] = rc == L.DI_OK
     return H, res, out
+
+
+def autotune(graph: Graph, d: float = 0.85, tol: float = 1e-9, precision: int = 0, budget: int = 20,
+             cache: str | None = None):
+    """Time candidate launch shapes on this graph and return (options dict for
+    State.solve / solve, report dict).  See di_autotune in include/di.h."""
+    o = L.di_opts()
+    b, dm = ctypes.c_double(), ctypes.c_double()
+    tr = ctypes.c_int32()
+    L.check(L.lib().di_autotune(graph.handle, d, tol, precision, budget,
+                                None if cache is None else cache.encode(), ctypes.byref(o), ctypes.byref(b),
+                                ctypes.byref(dm), ctypes.byref(tr), _stream()), "di_autotune")
+    opts = {k: getattr(o, k) for k in ("theta_factor", "hub_deg", "piece", "refine_ratio", "precision")}
+    return opts, {"best_ms": b.value, "default_ms": dm.value, "trials": tr.value}
