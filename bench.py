@@ -190,7 +190,7 @@ def adjoint_leg(torch, di, reps=4):
     return out
 
 
-def batch_leg(torch, di, peak, reps=3):
+def batch_leg(torch, di, peak, reps=3, union=True):
     """Batched personalised solves and uneven independent graphs.
 
     (a) 64 teleport vectors, each uniform over 1 to 1000 random seed pages, on
@@ -229,8 +229,11 @@ def batch_leg(torch, di, peak, reps=3):
            "worst_resid_l1": info["resid_l1"], "single_f64_total_ms": sum(single),
            "speedup_vs_single_f64": sum(single) / batch_ms,
            "k_bpush": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                       "traffic": traffic_for("bpush_web1m_traffic.json"),
                        "bytes_per_link": 260.0, "links_per_launch": links_per_launch,
                        "push_ms_avg": 1e3 * push_s, "launches": prof["push_launches"]}}
+    if not union:
+        return out
     # (b) uneven graphs
     gs = [synth.cached(synth.web_graph, n=nk, m_target=8 * nk, seed_offset=7000 + k, deg_hi=min(50_000, nk - 1))
           for k, nk in enumerate(synth.rng_for(77).integers(1_000, 50_001, size=256).tolist())]
@@ -266,14 +269,19 @@ def oracle_x(g, cp, ci):
     return H
 
 
-def traffic_for(kernel_src: str, precision: str):
-    """DRAM traffic per push launch from the committed ncu summary, if it was
-    taken on the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", f"push_web4m_{precision}_traffic.json")
+def traffic_for(record: str):
+    """DRAM traffic per launch from a committed ncu record (profiles/<record>),
+    if the kernel's source section is still the one the counters were taken on
+    (else None)."""
+    path = os.path.join(ROOT, "profiles", record)
     if not os.path.exists(path):
         return None
     rec = json.load(open(path))
-    h = hashlib.sha1(open(kernel_src, "rb").read()).hexdigest()
+    src = open(os.path.join(ROOT, rec["source_file"])).read()
+    a, b = rec["source_section"]
+    if a not in src or b not in src:
+        return None
+    h = hashlib.sha1(src[src.index(a):src.index(b)].encode()).hexdigest()
     return rec.get("dram_bytes_per_launch") if rec.get("source_sha1") == h else None
 
 
@@ -326,6 +334,9 @@ def main():
                     help="time the step with the library defaults instead of the autotuned options")
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the batched personalised solve and the union of 256 small graphs")
+    ap.add_argument("--no-union", action="store_true", help="batched leg without the union of 256 graphs")
+    ap.add_argument("--batch-only", action="store_true",
+                    help="run only the batched leg (for profiling) and print it as the JSON line")
     args = ap.parse_args()
     if args.warmup < 3 and not args.small:
         ap.error("--warmup must be >= 3")
@@ -344,6 +355,13 @@ def main():
     import torch
     import torch.distributed as dist
     torch.cuda.set_device(local)
+    if args.batch_only:
+        from paper_1501_06350_gb300 import di as di_mod
+        pk = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+            os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+        print(json.dumps({"batch": batch_leg(torch, di_mod, pk.get("hbm_gbs", 6800.0), union=not args.no_union)}),
+              flush=True)
+        return 0
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_1501_06350_gb300 import _lib, di
@@ -446,7 +464,7 @@ def main():
         peaks = json.load(open(pk_path))
     peak = peaks.get("hbm_gbs", 6800.0)
     achieved = alg_bytes / push_avg_s / 1e9
-    traffic = traffic_for(os.path.join(ROOT, "paper_1501_06350_gb300", "csrc", "di_solve.cu"), args.precision)
+    traffic = traffic_for(f"push_web4m_{args.precision}_traffic.json")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "kernel": "k_push<float>" if args.precision == "f32" else "k_push<double>",
@@ -486,7 +504,7 @@ def main():
     if rank == 0 and not args.no_adjoint:
         out["adjoint"] = adjoint_leg(torch, di)
     if rank == 0 and not args.no_batch:
-        out["batch"] = batch_leg(torch, di, peak)
+        out["batch"] = batch_leg(torch, di, peak, union=not args.no_union)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
