@@ -190,6 +190,56 @@ def adjoint_leg(torch, di, reps=4):
     return out
 
 
+def update50m_leg(torch, di, reps=2):
+    """The dynamic update at scale: a host-structured graph of 50,000,000 pages
+    and about 600,000,000 links drawn on the GPU (synth.web_graph_device, 1.05e9
+    draws merged), d = 0.85, uniform Z, tol 1e-9.  From-scratch solves in both
+    forms, then a 1% link batch (half deletions of existing links, half new
+    random links) injected (Section 3.5) and re-converged in the FP32 form, against
+    a from-scratch FP32 solve of the new graph.  Device times (CUDA events)."""
+    t0 = time.time()
+    ptr, idx = synth.web_graph_device(50_000_000, 1_050_000_000)
+    G = di.Graph(50_000_000, ptr, idx)
+    del ptr, idx
+    torch.cuda.empty_cache()
+    torch.cuda.synchronize()
+    setup_s = time.time() - t0
+    gi = G.info()
+    st = di.State(G)
+    out = {"workload": "host-structured web graph drawn on the GPU: 50,000,000 pages, %d links (int32 CSR), "
+                       "d=0.85, uniform Z, tol 1e-9; 1%% link changes (half deletions, half insertions)" % gi["nnz"],
+           "pages": gi["n"], "links": gi["nnz"], "dangling": gi["n_dangling"], "generate_and_build_s": setup_s}
+    for name, kw in (("f64", {}), ("f32_refined", {"precision": 1})):
+        ts, info = [], None
+        for _ in range(reps):
+            _, info = st.solve(D, tol=TOL, **kw)
+            ts.append(info["time_ms"])
+        out["from_scratch_" + name] = {"time_to_tol_ms": min(ts), "sweeps": info["sweeps"],
+                                       "edge_pushes": info["edge_pushes"],
+                                       "edge_pushes_per_s": info["edge_pushes"] / (min(ts) / 1e3)}
+    cp, ci, _ = G.export_csr(device=True, weights=False)
+    src, dst, op = synth.edge_batch_device(cp, ci, gi["n"], 0.01, 5)
+    del cp, ci
+    st.solve(D, tol=TOL, precision=1)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    st.update_edges(src, dst, op)
+    e1.record()
+    torch.cuda.synchronize()
+    _, ri = st.resume(tol=TOL, precision=1)
+    st2 = di.State(G)
+    _, si = st2.solve(D, tol=TOL, precision=1)
+    out["update"] = {"batch_links": int(src.numel()), "inject_and_patch_ms": e0.elapsed_time(e1),
+                     "reconverge_ms": ri["time_ms"], "reconverge_pushes": ri["edge_pushes"],
+                     "from_scratch_new_graph_ms": si["time_to_tol_ms"] if "time_to_tol_ms" in si else si["time_ms"],
+                     "from_scratch_new_graph_pushes": si["edge_pushes"],
+                     "update_vs_scratch_time": (e0.elapsed_time(e1) + ri["time_ms"]) / si["time_ms"]}
+    st.close()
+    st2.close()
+    G.close()
+    return out
+
+
 def batch_leg(torch, di, peak, reps=3, union=True):
     """Batched personalised solves and uneven independent graphs.
 
@@ -335,6 +385,8 @@ def main():
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the batched personalised solve and the union of 256 small graphs")
     ap.add_argument("--no-union", action="store_true", help="batched leg without the union of 256 graphs")
+    ap.add_argument("--update50m", action="store_true",
+                    help="run only the dynamic update on the 50M-page / ~600M-link graph and print it")
     ap.add_argument("--batch-only", action="store_true",
                     help="run only the batched leg (for profiling) and print it as the JSON line")
     args = ap.parse_args()
@@ -355,6 +407,10 @@ def main():
     import torch
     import torch.distributed as dist
     torch.cuda.set_device(local)
+    if args.update50m:
+        from paper_1501_06350_gb300 import di as di_mod
+        print(json.dumps({"update50m": update50m_leg(torch, di_mod)}), flush=True)
+        return 0
     if args.batch_only:
         from paper_1501_06350_gb300 import di as di_mod
         pk = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(

@@ -426,3 +426,101 @@ def exact_batch(ptr: np.ndarray, idx: np.ndarray, n: int, frac: float, seed_offs
     op = np.concatenate([-np.ones(len(ds), np.int8), np.ones(k, np.int8)])
     perm = rng.permutation(len(src))
     return src[perm], dst[perm], op[perm]
+
+
+def web_graph_device(n: int, m_target: int, dangling_frac: float = 0.15, host_mean: float = 100.0,
+                     host_sigma: float = 1.0, intra: float = 0.80, alpha: float = 2.1, deg_hi: int = 50_000,
+                     in_tail: float = 1.1, seed_offset: int = 50, device: str = "cuda"):
+    """Host-structured web-like graph drawn on the GPU with torch, for sizes whose
+    NumPy generation would take many minutes (tens of millions of pages).
+
+    Same recipe as ``web_graph`` (hosts of lognormal size with consecutive ids,
+    ``intra`` of the links inside the host, ``dangling_frac`` pages without
+    links, Zipf(alpha) out-degrees on [1, deg_hi] scaled to ``m_target``), with
+    two simplifications: a link's target is drawn by inverse-CDF sampling of a
+    power law over the page ranks of its host (intra-host) or of the whole
+    graph (the rest), P(rank k) ~ k^(-1/in_tail) (an in-degree tail of exponent
+    1 + in_tail), so low ids inside a host and overall are the popular pages;
+    and repeated links are left to the builders' merge.
+    Returns (ptr int64 [n+1], idx int32 [links]) as device tensors."""
+    import torch
+    gen = torch.Generator(device=device).manual_seed(150106350 + seed_offset)
+    # hosts: consecutive id ranges of lognormal size
+    mu = np.log(host_mean) - 0.5 * host_sigma ** 2
+    est = int(1.3 * n / host_mean) + 16
+    sizes = torch.exp(mu + host_sigma * torch.randn(est, generator=gen, device=device, dtype=torch.float64))
+    sizes = torch.clamp(torch.round(sizes), min=1).to(torch.int64)
+    ends = torch.cumsum(sizes, 0)
+    nh = int(torch.searchsorted(ends, torch.tensor([n], device=device)).item()) + 1
+    ends = ends[:nh].clone()
+    ends[-1] = n
+    starts = torch.cat([torch.zeros(1, dtype=torch.int64, device=device), ends[:-1]])
+    # out-degrees: Zipf(alpha) on [1, deg_hi] by inverse CDF, dangling pages 0, scaled to m_target
+    u = torch.rand(n, generator=gen, device=device, dtype=torch.float64)
+    a1 = 1.0 - alpha
+    lo, hi = 1.0, float(deg_hi) + 1.0
+    deg = torch.floor((lo ** a1 + u * (hi ** a1 - lo ** a1)) ** (1.0 / a1))
+    dang = torch.rand(n, generator=gen, device=device) < dangling_frac
+    deg = torch.where(dang, torch.zeros_like(deg), deg)
+    deg = deg * (m_target / float(deg.sum().item()))
+    deg = torch.floor(deg + torch.rand(n, generator=gen, device=device, dtype=torch.float64))
+    deg = torch.where(dang, torch.zeros_like(deg), torch.clamp(deg, min=1, max=deg_hi)).to(torch.int64)
+    ptr = torch.zeros(n + 1, dtype=torch.int64, device=device)
+    ptr[1:] = torch.cumsum(deg, 0)
+    m = int(ptr[-1].item())
+    src_all = torch.repeat_interleave(torch.arange(n, device=device), deg, output_size=m)
+    hsize = ends - starts
+    one_s = 1.0 - 1.0 / in_tail
+    big = torch.pow(torch.tensor(n + 1.0, device=device, dtype=torch.float64), one_s) - 1.0
+    out = torch.empty(m, dtype=torch.int32, device=device)
+    chunk = 1 << 27                              # links per chunk: bounds the temporaries
+    for c0 in range(0, m, chunk):
+        src = src_all[c0:c0 + chunk]
+        k = src.numel()
+        host = torch.searchsorted(ends, src, right=True)
+        h0, hs = starts[host], hsize[host]
+        del host
+        # rank k (1-based) with P(k) ~ k^-s, s = 1/in_tail, by the inverse CDF of the
+        # continuous law on [1, N + 1): k = (1 + u ((N+1)^(1-s) - 1))^(1/(1-s))
+        v = torch.rand(k, generator=gen, device=device, dtype=torch.float64)
+        inside = torch.rand(k, generator=gen, device=device) < intra
+        span = torch.pow(hs.to(torch.float64) + 1.0, one_s) - 1.0
+        r_in = torch.pow(1.0 + v * span, 1.0 / one_s).to(torch.int64) - 1
+        del span
+        tgt = h0 + torch.minimum(torch.clamp(r_in, min=0), hs - 1)
+        del r_in
+        r_out = torch.clamp(torch.pow(1.0 + v * big, 1.0 / one_s).to(torch.int64) - 1, min=0, max=n - 1)
+        tgt = torch.where(inside, tgt, r_out)
+        del r_out, v
+        # no self-links: move to the next page of the host (or of the graph)
+        same = tgt == src
+        tgt = torch.where(same & inside, h0 + torch.remainder(tgt - h0 + 1, hs), tgt)
+        tgt = torch.where(same & ~inside, torch.remainder(tgt + 1, n), tgt)
+        out[c0:c0 + k] = tgt.to(torch.int32)
+        del same, tgt, h0, hs, inside, src
+    del src_all
+    return ptr, out
+
+
+def edge_batch_device(ptr, idx, n: int, frac: float, seed_offset: int):
+    """``frac`` of the links changed, half deletions of existing links and half
+    insertions of random new pairs (no self-link), drawn on the GPU; returns
+    (src, dst, op) device tensors in random order."""
+    import torch
+    gen = torch.Generator(device=idx.device).manual_seed(4500 + seed_offset)
+    m = int(ptr[-1].item())
+    k = max(1, int(round(frac * m)))
+    nd = k // 2
+    ni = k - nd
+    pick = torch.randint(0, m, (nd,), generator=gen, device=idx.device)
+    ds = torch.searchsorted(ptr, pick, right=True) - 1
+    dd = idx[pick].to(torch.int64)
+    is_ = torch.randint(0, n, (ni,), generator=gen, device=idx.device)
+    id_ = torch.randint(0, n, (ni,), generator=gen, device=idx.device)
+    id_ = torch.where(is_ == id_, torch.remainder(id_ + 1, n), id_)
+    src = torch.cat([ds, is_])
+    dst = torch.cat([dd, id_])
+    op = torch.cat([-torch.ones(nd, dtype=torch.int8, device=idx.device),
+                    torch.ones(ni, dtype=torch.int8, device=idx.device)])
+    perm = torch.randperm(k, generator=gen, device=idx.device)
+    return src[perm].to(torch.int32), dst[perm].to(torch.int32), op[perm]
