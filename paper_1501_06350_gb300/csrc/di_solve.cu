@@ -834,6 +834,11 @@ __global__ void __launch_bounds__(PUSH_THREADS)
     constexpr int Q = 4;
     __shared__ unsigned long long s_links[PUSH_THREADS / 32];
     __shared__ unsigned long long s_hot[HOT_K];   // FP64: fixed point, units of 2^-hot_shift; FP32: floats
+    // per warp, the current unit's 128 nodes: link offset of each node inside
+    // the unit's link list, its first link, its per-link value
+    __shared__ unsigned s_start[PUSH_THREADS / 32][32 * 4];
+    __shared__ Off s_row[PUSH_THREADS / 32][32 * 4];
+    __shared__ T s_val[PUSH_THREADS / 32][32 * 4];
     volatile DevCtl *vc = ctl;
     if (!vc->push_ready) return;
     // hot_scale bounds what this sweep adds into one page (see k_plan; fluid
@@ -916,24 +921,29 @@ __global__ void __launch_bounds__(PUSH_THREADS)
             const unsigned total = __shfl_sync(FULL, incl, 31);
             const unsigned excl = incl - tot;
             links += total;
-            auto lane_link = [&](unsigned e, Off &link, T &vj) {
-                int j = 0;
+            // park the unit's nodes in shared memory: a link then finds its
+            // node by a binary search over the 128 starts (shared loads, the
+            // lanes of a batch mostly read the same entries) instead of a
+            // search plus a dozen shuffles
+            const int wq = threadIdx.x >> 5;
+            __syncwarp();
+            s_start[wq][Q * lane] = excl;
+            s_start[wq][Q * lane + 1] = excl + c1;
+            s_start[wq][Q * lane + 2] = excl + c2;
+            s_start[wq][Q * lane + 3] = excl + c3;
 #pragma unroll
-                for (int step = 16; step > 0; step >>= 1) {
-                    const unsigned ex = __shfl_sync(FULL, excl, j + step);
-                    if (ex <= e) j += step;
-                }
-                const unsigned o = e - __shfl_sync(FULL, excl, j);
-                const unsigned a1 = __shfl_sync(FULL, c1, j), a2 = __shfl_sync(FULL, c2, j),
-                               a3 = __shfl_sync(FULL, c3, j);
-                const Off q0 = __shfl_sync(FULL, r[0], j), q1 = __shfl_sync(FULL, r[1], j),
-                          q2 = __shfl_sync(FULL, r[2], j), q3 = __shfl_sync(FULL, r[3], j);
-                const T v0 = __shfl_sync(FULL, val[0], j), v1 = __shfl_sync(FULL, val[1], j),
-                        v2 = __shfl_sync(FULL, val[2], j), v3 = __shfl_sync(FULL, val[3], j);
-                if (o < a1) { link = q0 + o; vj = v0; }
-                else if (o < a2) { link = q1 + (o - a1); vj = v1; }
-                else if (o < a3) { link = q2 + (o - a2); vj = v2; }
-                else { link = q3 + (o - a3); vj = v3; }
+            for (int k = 0; k < Q; k++) {
+                s_row[wq][Q * lane + k] = r[k];
+                s_val[wq][Q * lane + k] = val[k];
+            }
+            __syncwarp();
+            auto lane_link = [&](unsigned e, Off &link, T &vj) {
+                int k = 0;
+#pragma unroll
+                for (int step = 64; step > 0; step >>= 1)
+                    if (s_start[wq][k + step] <= e) k += step;
+                link = s_row[wq][k] + (e - s_start[wq][k]);
+                vj = s_val[wq][k];
             };
             scatter_links<T, WEIGHTED>(total, lane_link, pcol, w, w32, Fd, s_hot, hot_shift, keep, stream);
         } else {
