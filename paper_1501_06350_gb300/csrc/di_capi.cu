@@ -74,14 +74,8 @@ di_status opts_ok(const di_opts *o)
 di_status prepare(di_graph_s *g, di_state_s *st, cudaStream_t s)
 {
     if (st->prep_version == g->version) return DI_OK;
-    if (st->gexec) {
-        cudaGraphExecDestroy(st->gexec);
-        st->gexec = nullptr;
-    }
-    if (st->gexec32) {
-        cudaGraphExecDestroy(st->gexec32);
-        st->gexec32 = nullptr;
-    }
+    // the captured sweep loops read the moved buffers through the state's
+    // pointer block, rewritten by the next solve: they stay valid
     st->dscale_d = -1.0;
     DI_TRY(state_prepare_graph(g, st, s));
     st->prep_version = g->version;

@@ -147,6 +147,23 @@ struct DevCtl {
     unsigned int pad1;
 };
 
+// The buffers of a graph and a state that move when the graph is updated or
+// the degree bins change.  The sweep kernels read them from this block (one
+// copy per state in device memory, rewritten before every solve), so a
+// captured sweep loop stays valid across updates.
+struct GraphPtrs {
+    const uint32_t *rp;
+    const int32_t *pcol;
+    const double *w;
+    const float *w32;
+    unsigned *hub_list;
+    uint32_t *pc_row;
+    uint32_t *pc_len;
+    double *pc_val;
+    int nhot;
+    uint32_t piece;
+};
+
 struct di_state_s {
     di_graph_t g = nullptr;
     int device = 0;
@@ -190,6 +207,8 @@ struct di_state_s {
     double *tile_l = nullptr;
     DevCtl *ctl = nullptr;
     DevCtl *host_ctl = nullptr;    // pinned mirror
+    GraphPtrs *gp = nullptr;       // device copy of the moving buffers
+    GraphPtrs *host_gp = nullptr;  // pinned mirror
     // CUDA graph of the sweep loop
     cudaGraphExec_t gexec = nullptr;     // FP64 fluid sweep loop
     cudaGraphExec_t gexec32 = nullptr;   // FP32 fluid sweep loop
@@ -228,6 +247,7 @@ di_status check_finite(const double *v, int64_t n, bool *ok, cudaStream_t s);
 di_status state_alloc(di_state_s *st, cudaStream_t s);
 di_status state_prepare_graph(di_graph_s *g, di_state_s *st, cudaStream_t s);
 di_status state_set_bins(di_graph_s *g, di_state_s *st, int hub_deg, int piece, cudaStream_t s);
+di_status state_sync_ptrs(di_graph_s *g, di_state_s *st, cudaStream_t s);
 di_status autotune(di_graph_s *g, double d, double tol, int precision, int budget, const char *cache,
                    di_opts *best, double *best_ms, double *default_ms, int *trials, int *from_cache,
                    cudaStream_t s);

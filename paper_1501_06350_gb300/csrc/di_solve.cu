@@ -453,8 +453,8 @@ __device__ __forceinline__ unsigned theta_word(double th, const float *)
 template <typename T>
 __global__ void __launch_bounds__(SEL_THREADS)
     k_select(const T *F, int64_t n, unsigned *mask, const unsigned *__restrict__ hubbits,
-             unsigned *hub_list, unsigned *tile_cnt, unsigned *tile_diff, float *tile_l1f, unsigned *tile_maxf,
-             unsigned *tile_maxu, DevCtl *ctl, int use_cond, cudaGraphConditionalHandle cond,
+             const GraphPtrs *__restrict__ gp, unsigned *tile_cnt, unsigned *tile_diff, float *tile_l1f,
+             unsigned *tile_maxf, unsigned *tile_maxu, DevCtl *ctl, int use_cond, cudaGraphConditionalHandle cond,
              int32_t *sel_ids)
 {
     typedef typename FluidWord<T>::U U;
@@ -500,6 +500,7 @@ __global__ void __launch_bounds__(SEL_THREADS)
     }
     const unsigned bits = selm & ~hubw;   // taken by the push
     const unsigned hubs = selm & hubw;    // taken by the plan
+    unsigned *hub_list = gp->hub_list;
     // selected hubs: one list reservation per warp
     {
         const unsigned nh = __popc(hubs);
@@ -583,11 +584,10 @@ __global__ void __launch_bounds__(SEL_THREADS)
 // also subtracts the taken amount: F + d P D - D.
 template <typename T, bool SUB>
 __global__ void __launch_bounds__(SEL_THREADS)
-    k_plan(T *Ft, T *Fd, double *Hs, const Off *__restrict__ rp, const double *__restrict__ dscale, int64_t n,
-           int64_t ntiles, const unsigned *__restrict__ hub_list, Off *pc_row, Off *pc_len, double *pc_val,
-           const unsigned *tile_cnt, const unsigned *tile_diff, const float *tile_l1f,
+    k_plan(T *Ft, T *Fd, double *Hs, const GraphPtrs *__restrict__ gp, const double *__restrict__ dscale,
+           int64_t n, int64_t ntiles, const unsigned *tile_cnt, const unsigned *tile_diff, const float *tile_l1f,
            const unsigned *tile_maxf, const unsigned *tile_maxu, DevCtl *ctl, int use_cond,
-           cudaGraphConditionalHandle cond, unsigned long long *stats, Off piece)
+           cudaGraphConditionalHandle cond, unsigned long long *stats)
 {
     typedef typename FluidWord<T>::U U;
     constexpr int NW = SEL_THREADS / 32;
@@ -683,6 +683,11 @@ __global__ void __launch_bounds__(SEL_THREADS)
     __syncthreads();
     if (!s_go) return;
     // take the selected hubs: one thread each
+    const Off *__restrict__ rp = gp->rp;
+    const unsigned *__restrict__ hub_list = gp->hub_list;
+    Off *pc_row = gp->pc_row, *pc_len = gp->pc_len;
+    double *pc_val = gp->pc_val;
+    const Off piece = gp->piece;
     const unsigned long long nhub = vc->nhub;
     const unsigned long long stream = pol_first(), keep = pol_last();
     for (unsigned long long h = (unsigned long long)blockIdx.x * SEL_THREADS + threadIdx.x; h < nhub;
@@ -824,13 +829,18 @@ __device__ __forceinline__ void scatter_links(unsigned total, LinkOf lane_link, 
 // four by their running degrees.  Ft / Fd / Hs / SUB as for k_plan.
 template <typename T, bool WEIGHTED, bool SUB>
 __global__ void __launch_bounds__(PUSH_THREADS)
-    k_push(T *Ft, T *Fd, double *Hs, const Off *__restrict__ rp, const double *__restrict__ dscale,
-           const unsigned *__restrict__ mask, const Off *__restrict__ pc_row, const Off *__restrict__ pc_len,
-           const double *__restrict__ pc_val, int64_t ngroups, const int32_t *__restrict__ pcol,
-           const int32_t *__restrict__ hot_node, int nhot, const double *__restrict__ w,
-           const float *__restrict__ w32, DevCtl *ctl)
+    k_push(T *Ft, T *Fd, double *Hs, const GraphPtrs *__restrict__ gp, const double *__restrict__ dscale,
+           const unsigned *__restrict__ mask, int64_t ngroups, const int32_t *__restrict__ hot_node, DevCtl *ctl)
 {
     typedef typename FluidWord<T>::U U;
+    const Off *__restrict__ rp = gp->rp;
+    const Off *__restrict__ pc_row = gp->pc_row;
+    const Off *__restrict__ pc_len = gp->pc_len;
+    const double *__restrict__ pc_val = gp->pc_val;
+    const int32_t *__restrict__ pcol = gp->pcol;
+    const double *__restrict__ w = gp->w;
+    const float *__restrict__ w32 = gp->w32;
+    const int nhot = gp->nhot;
     constexpr int Q = 4;
     __shared__ unsigned long long s_links[PUSH_THREADS / 32];
     __shared__ unsigned long long s_hot[HOT_K];   // FP64: fixed point, units of 2^-hot_shift; FP32: floats
@@ -1061,15 +1071,25 @@ di_status state_set_bins(di_graph_s *g, di_state_s *st, int hub_deg, int piece, 
     if (hub_deg == st->hub_deg && piece == st->piece) return DI_OK;
     st->hub_deg = hub_deg;
     st->piece = piece;
-    if (st->gexec) {
-        cudaGraphExecDestroy(st->gexec);
-        st->gexec = nullptr;
-    }
-    if (st->gexec32) {
-        cudaGraphExecDestroy(st->gexec32);
-        st->gexec32 = nullptr;
-    }
     return state_prepare_graph(g, st, s);
+}
+
+// Write the current positions of the moving buffers into the state's block.
+di_status state_sync_ptrs(di_graph_s *g, di_state_s *st, cudaStream_t s)
+{
+    GraphPtrs *h = st->host_gp;
+    h->rp = static_cast<const Off *>(g->rp);
+    h->pcol = g->pcol;
+    h->w = g->w;
+    h->w32 = g->w32;
+    h->hub_list = st->hub_list;
+    h->pc_row = st->pc_row;
+    h->pc_len = st->pc_len;
+    h->pc_val = st->pc_val;
+    h->nhot = g->nhot;
+    h->piece = (Off)st->piece;
+    DI_CUDA(cudaMemcpyAsync(st->gp, h, sizeof(GraphPtrs), cudaMemcpyHostToDevice, s));
+    return DI_OK;
 }
 
 di_status state_alloc(di_state_s *st, cudaStream_t s)
@@ -1092,6 +1112,7 @@ di_status state_alloc(di_state_s *st, cudaStream_t s)
     DI_TRY(dalloc_t(&st->tile_l1, st->ntiles, s));
     DI_TRY(dalloc_t(&st->tile_l, st->ntiles, s));
     DI_TRY(dalloc_t(&st->ctl, 1, s));
+    DI_TRY(dalloc_t(&st->gp, 1, s));
     DI_TRY(dalloc_t(&st->stats, 2 * STAT_CAP, s));
     DI_CUDA(cudaMemsetAsync(st->ctl, 0, sizeof(DevCtl), s));
     DI_CUDA(cudaMemsetAsync(st->mask, 0, sizeof(unsigned) * (slots / 32), s));
@@ -1100,6 +1121,8 @@ di_status state_alloc(di_state_s *st, cudaStream_t s)
     DI_TRY(state_prepare_graph(g, st, s));
     DI_CUDA(cudaMallocHost(reinterpret_cast<void **>(&st->host_ctl), sizeof(DevCtl)));
     memset(st->host_ctl, 0, sizeof(DevCtl));
+    DI_CUDA(cudaMallocHost(reinterpret_cast<void **>(&st->host_gp), sizeof(GraphPtrs)));
+    memset(st->host_gp, 0, sizeof(GraphPtrs));
     DI_CUDA(cudaEventCreate(&st->ev0));
     DI_CUDA(cudaEventCreate(&st->ev1));
     DI_CUDA(cudaStreamSynchronize(s));
@@ -1114,9 +1137,11 @@ di_status state_free(di_state_s *st)
     if (st->gstream) cudaStreamDestroy(st->gstream);
     void *bufs[] = {st->F, st->H, st->dscale, st->mask, st->hubbits, st->hub_list, st->pc_row, st->pc_len,
                     st->pc_val, st->tile_cnt, st->tile_diff, st->tile_l1f, st->tile_maxf, st->tile_l1,
-                    st->tile_l, st->ctl, st->stats, st->F32, st->D, st->rctl, st->tile_maxu, st->tile_max};
+                    st->tile_l, st->ctl, st->stats, st->F32, st->D, st->rctl, st->tile_maxu, st->tile_max,
+                    st->gp};
     for (void *p : bufs) dfree(p, s);
     if (st->host_ctl) cudaFreeHost(st->host_ctl);
+    if (st->host_gp) cudaFreeHost(st->host_gp);
     if (st->host_rctl) cudaFreeHost(st->host_rctl);
     if (st->ev0) cudaEventDestroy(st->ev0);
     if (st->ev1) cudaEventDestroy(st->ev1);
@@ -1150,11 +1175,11 @@ static void launch_select(di_graph_s *g, di_state_s *st, const Sweep &w, cudaStr
 {
     if (w.kind == SW_F32)
         k_select<float><<<(unsigned)st->ntiles, SEL_THREADS, 0, s>>>(
-            static_cast<const float *>(w.Ft), g->n, st->mask, st->hubbits, st->hub_list, st->tile_cnt,
+            static_cast<const float *>(w.Ft), g->n, st->mask, st->hubbits, st->gp, st->tile_cnt,
             st->tile_diff, st->tile_l1f, st->tile_maxf, st->tile_maxu, w.ctl, use_cond, h, sel_ids);
     else
         k_select<double><<<(unsigned)st->ntiles, SEL_THREADS, 0, s>>>(
-            static_cast<const double *>(w.Ft), g->n, st->mask, st->hubbits, st->hub_list, st->tile_cnt,
+            static_cast<const double *>(w.Ft), g->n, st->mask, st->hubbits, st->gp, st->tile_cnt,
             st->tile_diff, st->tile_l1f, st->tile_maxf, st->tile_maxu, w.ctl, use_cond, h, sel_ids);
     count_launches(1);
 }
@@ -1162,11 +1187,10 @@ static void launch_select(di_graph_s *g, di_state_s *st, const Sweep &w, cudaStr
 static void launch_plan(di_graph_s *g, di_state_s *st, const Sweep &w, cudaStream_t s, int use_cond,
                         cudaGraphConditionalHandle h)
 {
-    const Off *rp = static_cast<const Off *>(g->rp);
     unsigned long long *stats = w.kind == SW_REFINE ? nullptr : st->stats;
-#define DI_PLAN_ARGS                                                                                      \
-    w.Hs, rp, st->dscale, g->n, st->ntiles, st->hub_list, st->pc_row, st->pc_len, st->pc_val, st->tile_cnt, \
-        st->tile_diff, st->tile_l1f, st->tile_maxf, st->tile_maxu, w.ctl, use_cond, h, stats, (Off)st->piece
+#define DI_PLAN_ARGS                                                                                   \
+    w.Hs, st->gp, st->dscale, g->n, st->ntiles, st->tile_cnt, st->tile_diff, st->tile_l1f, st->tile_maxf, \
+        st->tile_maxu, w.ctl, use_cond, h, stats
     if (w.kind == SW_F32)
         k_plan<float, false><<<PLAN_CTAS, SEL_THREADS, 0, s>>>(static_cast<float *>(w.Ft),
                                                                static_cast<float *>(w.Fd), DI_PLAN_ARGS);
@@ -1184,10 +1208,7 @@ static void launch_push(di_graph_s *g, di_state_s *st, const Sweep &w, cudaStrea
 {
     const int grid = push_grid(st->device, w.kind, g->weighted);
     const int64_t ngroups = st->ntiles * TILE / 32;
-    const Off *rp = static_cast<const Off *>(g->rp);
-#define DI_PUSH_ARGS                                                                                  \
-    w.Hs, rp, st->dscale, st->mask, st->pc_row, st->pc_len, st->pc_val, ngroups, g->pcol, g->hot_node, \
-        g->nhot, g->w, g->w32, w.ctl
+#define DI_PUSH_ARGS w.Hs, st->gp, st->dscale, st->mask, ngroups, g->hot_node, w.ctl
     float *f32t = static_cast<float *>(w.Ft), *f32d = static_cast<float *>(w.Fd);
     double *f64t = static_cast<double *>(w.Ft), *f64d = static_cast<double *>(w.Fd);
     if (w.kind == SW_F32) {
@@ -1372,6 +1393,7 @@ di_status solve_loop(di_graph_s *g, di_state_s *st, double tol, const di_opts *o
     const bool f32 = o->precision == DI_PREC_F32;
     if (f32) DI_TRY(state_alloc_f32(st, s));
     DI_TRY(state_set_bins(g, st, o->hub_deg, o->piece, s));
+    DI_TRY(state_sync_ptrs(g, st, s));
     if (fresh) {
         k_init<<<grid_for(n, 256), 256, 0, s>>>(st->F, st->H, Z_dev, n, 1.0 - d, 1.0 / (double)n);
         count_launches(1);
@@ -1578,6 +1600,7 @@ di_status select_only(di_graph_s *g, const double *F, double theta, int32_t *ids
             hc->theta_factor = 1.0;
             cudaMemcpyAsync(st.ctl, hc, sizeof(DevCtl), cudaMemcpyHostToDevice, s);
             cudaMemcpyAsync(st.F, F, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
+            state_sync_ptrs(g, &st, s);
             k_dscale<<<grid_for(n, 256), 256, 0, s>>>(static_cast<const Off *>(g->rp), g->wsum, n, 0.85,
                                                       st.dscale);
             count_launches(1);
