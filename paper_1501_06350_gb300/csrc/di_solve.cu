@@ -32,6 +32,7 @@
 #include <cuda_runtime.h>
 #include <new>
 #include <string.h>
+#include <vector>
 
 #include "di_internal.cuh"
 
@@ -1467,9 +1468,9 @@ di_status solve_loop(di_graph_s *g, di_state_s *st, double tol, const di_opts *o
     if (pp.npairs) {
         // push launch i follows selection i; selections past the converged
         // sweep returned at once and their pushes found no work
-        static unsigned long long hstats[2 * STAT_CAP];
+        std::vector<unsigned long long> hstats(2 * STAT_CAP);
         const int ran = (int)((int64_t)hc->sweep < pp.npairs ? (int64_t)hc->sweep : pp.npairs);
-        DI_CUDA(cudaMemcpy(hstats, st->stats, sizeof(unsigned long long) * 2 * ran, cudaMemcpyDeviceToHost));
+        DI_CUDA(cudaMemcpy(hstats.data(), st->stats, sizeof(unsigned long long) * 2 * ran, cudaMemcpyDeviceToHost));
         for (int i = 0; i < ran; i++) {
             if (hstats[2 * i] == 0) continue;
             float pm = 0.f;
