@@ -319,10 +319,10 @@ def oracle_x(g, cp, ci):
     return H
 
 
-def traffic_for(record: str):
+def traffic_for(record: str, opts: dict | None = None):
     """DRAM traffic per launch from a committed ncu record (profiles/<record>),
     if the kernel's source section is still the one the counters were taken on
-    (else None)."""
+    and the record's solver options match `opts` (else None)."""
     path = os.path.join(ROOT, "profiles", record)
     if not os.path.exists(path):
         return None
@@ -332,7 +332,14 @@ def traffic_for(record: str):
     if a not in src or b not in src:
         return None
     h = hashlib.sha1(src[src.index(a):src.index(b)].encode()).hexdigest()
-    return rec.get("dram_bytes_per_launch") if rec.get("source_sha1") == h else None
+    if rec.get("source_sha1") != h:
+        return None
+    if opts is not None:
+        taken = rec.get("options", {})
+        for k in ("theta_factor", "hub_deg", "piece"):
+            if k in opts and abs(float(taken.get(k, -1)) - float(opts[k])) > 1e-12:
+                return None
+    return rec.get("dram_bytes_per_launch")
 
 
 def forms(st, G, g, torch, x_ref, reps=5):
@@ -520,7 +527,9 @@ def main():
         peaks = json.load(open(pk_path))
     peak = peaks.get("hbm_gbs", 6800.0)
     achieved = alg_bytes / push_avg_s / 1e9
-    traffic = traffic_for(f"push_web4m_{args.precision}_traffic.json")
+    run_opts = {"theta_factor": sopt.get("theta_factor", 1.0), "hub_deg": sopt.get("hub_deg", 256),
+                "piece": sopt.get("piece", 1024)}
+    traffic = traffic_for(f"push_web4m_{args.precision}_c{run_opts['theta_factor']:g}_traffic.json", run_opts)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "kernel": "k_push<float>" if args.precision == "f32" else "k_push<double>",
