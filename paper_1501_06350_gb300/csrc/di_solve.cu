@@ -691,21 +691,40 @@ __global__ void __launch_bounds__(SEL_THREADS)
     const Off piece = gp->piece;
     const unsigned long long nhub = vc->nhub;
     const unsigned long long stream = pol_first(), keep = pol_last();
-    for (unsigned long long h = (unsigned long long)blockIdx.x * SEL_THREADS + threadIdx.x; h < nhub;
-         h += (unsigned long long)gridDim.x * SEL_THREADS) {
-        const unsigned i = hub_list[h];
-        const U fbits = ld_word(Ft + i, keep);
-        const Off r0 = ldnc_u32(rp + i, stream), r1 = ldnc_u32(rp + i + 1, stream);
-        const unsigned long long hb = ld_b64(Hs + i, stream);
-        const double ds = ldnc_f64(dscale + i, stream);
-        const double f = (double)word_val(fbits);
-        st_b64(Hs + i, (unsigned long long)__double_as_longlong(__longlong_as_double((long long)hb) + f), stream);
-        st_word(Ft + i, (U)0, keep);
-        if (SUB) red_add_f64(reinterpret_cast<double *>(Fd) + i, -f, keep);
-        const Off deg = r1 - r0;
-        const double v = f * ds;
-        const unsigned np = (deg + piece - 1) / piece;
-        unsigned long long pb = atomicAdd((unsigned long long *)&ctl->npieces, (unsigned long long)np);
+    // warps over 32 consecutive list entries; one piece-queue reservation per warp
+    for (unsigned long long h0 = ((unsigned long long)blockIdx.x * SEL_THREADS + threadIdx.x) & ~31ull; h0 < nhub;
+         h0 += (unsigned long long)gridDim.x * SEL_THREADS) {
+        const unsigned long long h = h0 + lane;
+        unsigned np = 0;
+        Off r0 = 0, deg = 0;
+        double v = 0.0;
+        if (h < nhub) {
+            const unsigned i = hub_list[h];
+            const U fbits = ld_word(Ft + i, keep);
+            r0 = ldnc_u32(rp + i, stream);
+            const Off r1 = ldnc_u32(rp + i + 1, stream);
+            const unsigned long long hb = ld_b64(Hs + i, stream);
+            const double ds = ldnc_f64(dscale + i, stream);
+            const double f = (double)word_val(fbits);
+            st_b64(Hs + i, (unsigned long long)__double_as_longlong(__longlong_as_double((long long)hb) + f),
+                   stream);
+            st_word(Ft + i, (U)0, keep);
+            if (SUB) red_add_f64(reinterpret_cast<double *>(Fd) + i, -f, keep);
+            deg = r1 - r0;
+            v = f * ds;
+            np = (deg + piece - 1) / piece;
+        }
+        unsigned incl = np;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const unsigned wtot = __shfl_sync(FULL, incl, 31);
+        unsigned long long wbase = 0;
+        if (lane == 31 && wtot) wbase = atomicAdd((unsigned long long *)&ctl->npieces, (unsigned long long)wtot);
+        wbase = __shfl_sync(FULL, wbase, 31);
+        unsigned long long pb = wbase + incl - np;
         for (Off o = 0; o < deg; o += piece) {
             pc_row[pb] = r0 + o;
             pc_len[pb] = deg - o < piece ? deg - o : piece;
