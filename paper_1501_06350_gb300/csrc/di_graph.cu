@@ -37,20 +37,44 @@ __global__ void k_validate(const int64_t *ptr, const int32_t *idx, const void *w
     if (e) atomicOr(err, e);
 }
 
-// One warp per input row: key = (source << 32 | target), value = input position.
-__global__ void k_make_keys(const int64_t *ptr, const int32_t *idx, int64_t n, int layout,
+// key = (source << 32 | target), value = input position, for every input
+// link.  One warp per 32 consecutive links (long rows are spread over many
+// warps): lanes 0 and 1 find the rows of the first and last link by binary
+// search over the row pointers, then every lane searches its own row inside
+// that short range.
+__global__ void k_make_keys(const int64_t *ptr, const int32_t *idx, int64_t n, int64_t nnz, int layout,
                             uint64_t *keys, uint32_t *vals)
 {
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t r = warp; r < n; r += nwarps) {
-        const int64_t a = ptr[r], b = ptr[r + 1];
-        for (int64_t e = a + lane; e < b; e += 32) {
-            const uint64_t c = (uint32_t)idx[e];
-            keys[e] = layout == DI_LAYOUT_CSR ? (((uint64_t)r << 32) | c) : ((c << 32) | (uint64_t)r);
-            vals[e] = (uint32_t)e;
+    const int64_t nchunks = (nnz + 31) / 32;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < nchunks; c += nw) {
+        const int64_t e0 = c * 32;
+        const int64_t last = e0 + 31 < nnz ? e0 + 31 : nnz - 1;
+        int64_t jr = 0;
+        if (lane < 2) {
+            const int64_t target = lane == 0 ? e0 : last;   // largest row r with ptr[r] <= target
+            int64_t lo = 0, hi = n - 1;
+            while (lo < hi) {
+                const int64_t mid = (lo + hi + 1) >> 1;
+                if (__ldg(ptr + mid) <= target) lo = mid;
+                else hi = mid - 1;
+            }
+            jr = lo;
         }
+        const int64_t rf = __shfl_sync(0xffffffffu, jr, 0), rl = __shfl_sync(0xffffffffu, jr, 1);
+        const int64_t e = e0 + lane;
+        if (e >= nnz) continue;
+        int64_t lo = rf, hi = rl;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) >> 1;
+            if (__ldg(ptr + mid) <= e) lo = mid;
+            else hi = mid - 1;
+        }
+        const uint64_t r = (uint64_t)lo;
+        const uint64_t t = (uint32_t)idx[e];
+        keys[e] = layout == DI_LAYOUT_CSR ? ((r << 32) | t) : ((t << 32) | r);
+        vals[e] = (uint32_t)e;
     }
 }
 
@@ -193,7 +217,7 @@ static di_status build(di_graph_s *g, int64_t n, int64_t nnz, const int64_t *ptr
     DI_TRY(t.get(&vals, nnz));
     DI_TRY(t.get(&vals2, nnz));
     if (nnz > 0) {
-        k_make_keys<<<grid_for(n * 32, 256), 256, 0, s>>>(ptr_d, idx_d, n, layout, keys, vals);
+        k_make_keys<<<grid_for(nnz, 256), 256, 0, s>>>(ptr_d, idx_d, n, nnz, layout, keys, vals);
         count_launches(1);
         DI_CUDA(cudaGetLastError());
         const int b = bits_for(n);
