@@ -885,19 +885,26 @@ __global__ void __launch_bounds__(PUSH_THREADS)
         vc->nhub = 0;                 // the plan has consumed the hub list
         vc->sweep = vc->sweep + 1;    // (the plan reads it; it is stable until here)
     }
-    const unsigned long long npc = vc->npieces;
+    // unit and piece counts stay below 2^32 (n / 128 units; pieces <= links)
+    const unsigned npc = (unsigned)vc->npieces;
     const unsigned long long keep = pol_last(), stream = pol_first();
     const int lane = threadIdx.x & 31;
-    const unsigned long long nunits = (unsigned long long)ngroups / Q;
-    const unsigned long long wid = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const unsigned long long nw = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
+    const unsigned nunits = (unsigned)(ngroups / Q);
+    const unsigned wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const unsigned nw = (gridDim.x * blockDim.x) >> 5;
     unsigned long long links = 0;
-    for (unsigned long long u = wid; u < nunits + npc; u += nw) {
+    // the mask word of the warp's next unit is loaded one unit ahead
+    unsigned mw_next = wid < nunits ? ldnc_u32(mask + (size_t)wid * Q + (lane >> 3), stream) : 0u;
+    for (unsigned u = wid; u < nunits + npc; u += nw) {
         if (u < nunits) {
-            const unsigned mw = ldnc_u32(mask + u * Q + (lane >> 3), stream);
+            const unsigned mw = mw_next;
+            {
+                const unsigned un = u + nw;
+                mw_next = un < nunits ? ldnc_u32(mask + (size_t)un * Q + (lane >> 3), stream) : 0u;
+            }
             const unsigned bits = (mw >> (Q * (lane & 7))) & ((1u << Q) - 1u);
             if (!__any_sync(FULL, bits)) continue;
-            const unsigned long long i0 = u * (32 * Q) + (unsigned long long)lane * Q;
+            const unsigned long long i0 = (unsigned long long)u * (32 * Q) + (unsigned long long)lane * Q;
             Off r[Q + 1];
             T val[Q];
             unsigned c1 = 0, c2 = 0, c3 = 0, tot = 0;
@@ -977,7 +984,7 @@ __global__ void __launch_bounds__(PUSH_THREADS)
             };
             scatter_links<T, WEIGHTED>(total, lane_link, pcol, w, w32, Fd, s_hot, hot_shift, keep, stream);
         } else {
-            const unsigned long long p = u - nunits;
+            const unsigned p = u - nunits;
             const Off row = ldnc_u32(pc_row + p, stream), len = ldnc_u32(pc_len + p, stream);
             const T pv = (T)ldnc_f64(pc_val + p, stream);
             links += len;
