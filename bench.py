@@ -565,7 +565,7 @@ def main():
            "wall_s": wall, "gpu_launches": int(launches), "clocks": clk, "roofline": roofline}
 
     if rank == 0 and world == 1 and not args.no_e2e:
-        out["e2e"] = e2e(args, g, src, dst, op, di, torch)
+        out["e2e"] = e2e(args, g, src, dst, op, di, torch, sopt)
     x_ref = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(g, cp, ci)
@@ -586,9 +586,10 @@ def main():
     return 0
 
 
-def e2e(args, g, src, dst, op, di, torch):
+def e2e(args, g, src, dst, op, di, torch, sopt):
     """Same step through the public API with host buffers: graph upload from
-    pinned host memory, host Z in, host H out after every solve."""
+    pinned host memory, host Z in, host H out after every solve (with the
+    solver options of the device-timed step)."""
     def pinned(a):
         t = torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
         return t.numpy()
@@ -601,11 +602,11 @@ def e2e(args, g, src, dst, op, di, torch):
         t = time.perf_counter()
         G = di.Graph(g.n, ptr, idx)
         st = di.State(G)
-        _, i1 = st.solve(D, Z=Z, tol=TOL, out=Hh, device=False)
+        _, i1 = st.solve(D, Z=Z, tol=TOL, out=Hh, device=False, **sopt)
         st.update_edges(s, d_, o)
-        _, i2 = st.resume(tol=TOL, out=Hh, device=False)
+        _, i2 = st.resume(tol=TOL, out=Hh, device=False, **sopt)
         st.update_edges(s, d_, oi)
-        _, i3 = st.resume(tol=TOL, out=Hh, device=False)
+        _, i3 = st.resume(tol=TOL, out=Hh, device=False, **sopt)
         dt = time.perf_counter() - t
         st.close()
         G.close()
@@ -616,7 +617,8 @@ def e2e(args, g, src, dst, op, di, torch):
     d2h = 3 * Hh.nbytes
     return {"value": sum(pushes) / sum(times), "unit": METRIC, "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * sum(times) / len(times),
-            "includes": "graph build from pinned host CSR, state setup, 3 solves with host Z/H, 2 updates"}
+            "includes": "graph build from pinned host CSR, state setup, 3 solves with host Z/H, 2 updates",
+            "options": dict(sopt)}
 
 
 if __name__ == "__main__":

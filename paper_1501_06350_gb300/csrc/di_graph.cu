@@ -37,35 +37,33 @@ __global__ void k_validate(const int64_t *ptr, const int32_t *idx, const void *w
     if (e) atomicOr(err, e);
 }
 
-// key = (source << 32 | target), value = input position, for every input
-// link.  One warp per 32 consecutive links (long rows are spread over many
-// warps): lanes 0 and 1 find the rows of the first and last link by binary
-// search over the row pointers, then every lane searches its own row inside
-// that short range.
-__global__ void k_make_keys(const int64_t *ptr, const int32_t *idx, int64_t n, int64_t nnz, int layout,
-                            uint64_t *keys, uint32_t *vals)
+// Row lookup table for the link-parallel key construction: tab[q] is the row
+// holding link q * 2^KEY_BUCKET_SHIFT (each such link lies in exactly one
+// non-empty row, which writes it); tab[nbk] = n - 1.
+constexpr int KEY_BUCKET_SHIFT = 8;
+__global__ void k_bucket_rows(const int64_t *ptr, int64_t n, int64_t nbk, uint32_t *tab)
 {
-    const int lane = threadIdx.x & 31;
-    const int64_t nchunks = (nnz + 31) / 32;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < nchunks; c += nw) {
-        const int64_t e0 = c * 32;
-        const int64_t last = e0 + 31 < nnz ? e0 + 31 : nnz - 1;
-        int64_t jr = 0;
-        if (lane < 2) {
-            const int64_t target = lane == 0 ? e0 : last;   // largest row r with ptr[r] <= target
-            int64_t lo = 0, hi = n - 1;
-            while (lo < hi) {
-                const int64_t mid = (lo + hi + 1) >> 1;
-                if (__ldg(ptr + mid) <= target) lo = mid;
-                else hi = mid - 1;
-            }
-            jr = lo;
-        }
-        const int64_t rf = __shfl_sync(0xffffffffu, jr, 0), rl = __shfl_sync(0xffffffffu, jr, 1);
-        const int64_t e = e0 + lane;
-        if (e >= nnz) continue;
-        int64_t lo = rf, hi = rl;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t a = ptr[r], b = ptr[r + 1];
+        if (a >= b) continue;
+        const int64_t q0 = (a + (1 << KEY_BUCKET_SHIFT) - 1) >> KEY_BUCKET_SHIFT;
+        const int64_t q1 = (b - 1) >> KEY_BUCKET_SHIFT;
+        for (int64_t q = q0; q <= q1; q++) tab[q] = (uint32_t)r;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) tab[nbk] = (uint32_t)(n - 1);
+}
+
+// key = (source << 32 | target), value = input position, for every input
+// link, one thread per link: the row of link e is the largest r with
+// ptr[r] <= e, searched between the rows of the bucket starts around e.
+__global__ void k_make_keys(const int64_t *ptr, const int32_t *idx, int64_t n, int64_t nnz, int layout,
+                            const uint32_t *tab, uint64_t *keys, uint32_t *vals)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t q = e >> KEY_BUCKET_SHIFT;
+        int64_t lo = __ldg(tab + q), hi = __ldg(tab + q + 1);   // ptr[lo] <= e, row(e) <= hi
         while (lo < hi) {
             const int64_t mid = (lo + hi + 1) >> 1;
             if (__ldg(ptr + mid) <= e) lo = mid;
@@ -150,7 +148,10 @@ __global__ void k_row_sums(const uint32_t *rp, const double *w, int64_t n, doubl
             wsum[j] = s;
         }
     }
-    if (c) atomicAdd(ndang, c);
+    // one atomic per warp (one counter for the whole grid)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(ndang, c);
 }
 
 __global__ void k_expand_rows(const uint32_t *rp, int64_t n, const int32_t *col, uint64_t *keys,
@@ -217,8 +218,12 @@ static di_status build(di_graph_s *g, int64_t n, int64_t nnz, const int64_t *ptr
     DI_TRY(t.get(&vals, nnz));
     DI_TRY(t.get(&vals2, nnz));
     if (nnz > 0) {
-        k_make_keys<<<grid_for(nnz, 256), 256, 0, s>>>(ptr_d, idx_d, n, nnz, layout, keys, vals);
-        count_launches(1);
+        const int64_t nbk = (nnz + (1 << KEY_BUCKET_SHIFT) - 1) >> KEY_BUCKET_SHIFT;
+        uint32_t *tab;
+        DI_TRY(t.get(&tab, nbk + 1));
+        k_bucket_rows<<<grid_for(n, 256), 256, 0, s>>>(ptr_d, n, nbk, tab);
+        k_make_keys<<<grid_for(nnz, 256), 256, 0, s>>>(ptr_d, idx_d, n, nnz, layout, tab, keys, vals);
+        count_launches(2);
         DI_CUDA(cudaGetLastError());
         const int b = bits_for(n);
         int lo[16], cnt[16], np = 0;
@@ -473,6 +478,7 @@ di_status graph_export(di_graph_s *g, bool csc, int64_t *ptr, int32_t *idx, doub
 di_status graph_create(int64_t n, int64_t nnz, const int64_t *ptr, const int32_t *idx, const void *w,
                        int wdt, int layout, int mem, cudaStream_t s, di_graph_s *g)
 {
+    pool_keep(g->device);
     Temps t(s);
     const int64_t *ptr_d = ptr;
     const int32_t *idx_d = idx;

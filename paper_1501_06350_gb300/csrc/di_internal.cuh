@@ -28,6 +28,7 @@ di_status note_cuda(cudaError_t e);          // records e for di_last_cuda_error
 // Stream-ordered device allocation; returns DI_ERR_OOM on failure.
 di_status dalloc(void **p, size_t bytes, cudaStream_t s);
 void dfree(void *p, cudaStream_t s);
+void pool_keep(int device);   // keep freed scratch in the default pool (once per device)
 
 template <typename T>
 di_status dalloc_t(T **p, size_t count, cudaStream_t s)

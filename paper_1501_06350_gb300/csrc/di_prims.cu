@@ -40,6 +40,25 @@ void dfree(void *p, cudaStream_t s)
     if (p) cudaFreeAsync(p, s);
 }
 
+// The library's scratch comes from the device's default stream-ordered pool.
+// By default the pool returns freed memory to the driver at every
+// synchronisation, so each graph build, update or solve with host inputs
+// mapped and unmapped its temporaries again (about 3 ms of a 4M-page build).
+// Keeping up to POOL_KEEP bytes of freed memory in the pool (an attribute of
+// this process's pool, gone with the process) lets them be reused.
+constexpr uint64_t POOL_KEEP = 2ull << 30;
+void pool_keep(int device)
+{
+    static bool done[64] = {};
+    if (device < 0 || device >= 64 || done[device]) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+        uint64_t keep = POOL_KEEP;
+        if (cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep) == cudaSuccess) done[device] = true;
+    }
+    cudaGetLastError();
+}
+
 int sm_count(int device)
 {
     int v = 0;
@@ -165,10 +184,17 @@ template di_status scan_exclusive<uint32_t>(const uint32_t *, uint64_t *, int64_
 template di_status scan_exclusive<uint64_t>(const uint64_t *, uint64_t *, int64_t, uint64_t *, cudaStream_t);
 
 // ------------------------------------------------------------- radix sort
+// One LSD pass = a per-tile digit histogram, an exclusive scan of the
+// histograms in (digit, tile) order, and a stable scatter.  A tile is 2048
+// pairs; warp w of its CTA holds the tile's items [256 w, 256 w + 256) with
+// item k of lane l at 256 w + 32 k + l, so walking k-major inside a warp and
+// warps in order visits the tile in index order.
 constexpr int RS_NT = 256;
-constexpr int RS_ITEMS = 16;
+constexpr int RS_ITEMS = 8;
 constexpr int RS_TILE = RS_NT * RS_ITEMS;
 constexpr int RS_WARPS = RS_NT / 32;
+constexpr int RS_WITEMS = RS_ITEMS * 32;
+static_assert(RS_NT == 256, "one digit per thread");
 
 __global__ void __launch_bounds__(RS_NT) k_radix_hist(const uint64_t *keys, int64_t n, int shift,
                                                      int nbits, int64_t ntiles, uint32_t *hist)
@@ -188,59 +214,100 @@ __global__ void __launch_bounds__(RS_NT) k_radix_hist(const uint64_t *keys, int6
     if (threadIdx.x < ndig) hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = cnt[threadIdx.x];
 }
 
-// Stable scatter: keys of the tile are ranked in index order (item k of
-// thread t is index k*RS_NT + t, so items are walked k-major, warps in order,
-// lanes in order).
+// Stable scatter.  Every item gets its rank among the tile's items of the same
+// digit (index order: within a warp by item and lane, __match_any_sync groups
+// the lanes of one digit; warps in order through per-warp counts); the tile is
+// reordered by digit in shared memory and written out with consecutive
+// threads writing consecutive positions of each digit's run.
 __global__ void __launch_bounds__(RS_NT) k_radix_scatter(const uint64_t *kin, const uint32_t *vin,
                                                         uint64_t *kout, uint32_t *vout, int64_t n,
                                                         int shift, int nbits, int64_t ntiles,
                                                         const uint64_t *offs)
 {
-    __shared__ uint32_t s_wcnt[RS_WARPS][256];
-    __shared__ uint32_t s_run[256];
-    __shared__ uint64_t s_base[256];
+    __shared__ uint64_t s_key[RS_TILE];
+    __shared__ uint32_t s_val[RS_TILE];
+    __shared__ uint32_t s_wcnt[RS_WARPS][256];   // per-warp digit counts, then offsets
+    __shared__ uint32_t s_dstart[256];           // tile-local start of each digit's run
+    __shared__ uint32_t s_wsum[RS_WARPS];
+    __shared__ uint64_t s_gbase[256];            // global start of the run of each digit
     const int ndig = 1 << nbits;
     const uint64_t mask = (uint64_t)ndig - 1;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
-    s_run[threadIdx.x] = 0;
-    if (threadIdx.x < ndig) s_base[threadIdx.x] = offs[(int64_t)threadIdx.x * ntiles + blockIdx.x];
-    const int64_t base = (int64_t)blockIdx.x * RS_TILE;
-    for (int k = 0; k < RS_ITEMS; k++) {
-        const int64_t i = base + (int64_t)k * RS_NT + threadIdx.x;
-        const bool valid = i < n;
-        uint64_t key = 0;
-        uint32_t val = 0;
-        int dg = 256;  // sentinel for past-the-end slots
-        if (valid) {
-            key = kin[i];
-            val = vin[i];
-            dg = (int)((key >> shift) & mask);
-        }
-        const unsigned peers = __match_any_sync(FULL, dg);
-        const unsigned lrank = __popc(peers & lt);
-        for (int q = lane; q < 256; q += 32) s_wcnt[warp][q] = 0;
-        __syncwarp();
-        if (valid && lrank == 0) s_wcnt[warp][dg] = __popc(peers);
-        __syncthreads();
-        {
-            const int dgt = threadIdx.x;  // one digit per thread (RS_NT == 256)
-            uint32_t run = s_run[dgt];
+    for (int q = threadIdx.x; q < RS_WARPS * 256; q += RS_NT) (&s_wcnt[0][0])[q] = 0;
+    s_gbase[threadIdx.x] = threadIdx.x < ndig ? offs[(int64_t)threadIdx.x * ntiles + blockIdx.x] : 0ull;
+    __syncthreads();
+    const int64_t t0 = (int64_t)blockIdx.x * RS_TILE;
+    const int64_t w0 = t0 + (int64_t)warp * RS_WITEMS;
+    uint64_t key[RS_ITEMS];
+    uint32_t val[RS_ITEMS];
+    int dg[RS_ITEMS];
+    uint32_t rk[RS_ITEMS];
 #pragma unroll
-            for (int w = 0; w < RS_WARPS; w++) {
-                uint32_t c = s_wcnt[w][dgt];
-                s_wcnt[w][dgt] = run;
-                run += c;
-            }
-            s_run[dgt] = run;
+    for (int k = 0; k < RS_ITEMS; k++) {
+        const int64_t i = w0 + 32 * k + lane;
+        key[k] = 0;
+        val[k] = 0;
+        dg[k] = 256;   // past the end
+        if (i < n) {
+            key[k] = kin[i];
+            val[k] = vin[i];
+            dg[k] = (int)((key[k] >> shift) & mask);
         }
-        __syncthreads();
-        if (valid) {
-            const uint64_t pos = s_base[dg] + s_wcnt[warp][dg] + lrank;
-            kout[pos] = key;
-            vout[pos] = val;
+    }
+#pragma unroll
+    for (int k = 0; k < RS_ITEMS; k++) {
+        const unsigned peers = __match_any_sync(FULL, dg[k]);
+        const int leader = __ffs(peers) - 1;
+        uint32_t before = 0;
+        if (lane == leader && dg[k] < 256) {
+            // only this lane touches this warp's count of this digit now
+            before = s_wcnt[warp][dg[k]];
+            s_wcnt[warp][dg[k]] = before + (uint32_t)__popc(peers);
         }
+        before = __shfl_sync(FULL, before, leader);
+        rk[k] = before + (uint32_t)__popc(peers & lt);
+    }
+    __syncthreads();
+    // per digit (one per thread): offsets of the warps, then the tile's runs
+    {
+        const int d = threadIdx.x;
+        uint32_t run = 0;
+#pragma unroll
+        for (int w = 0; w < RS_WARPS; w++) {
+            const uint32_t c = s_wcnt[w][d];
+            s_wcnt[w][d] = run;
+            run += c;
+        }
+        uint32_t incl = run;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) s_wsum[warp] = incl;
         __syncthreads();
+        uint32_t prev = 0;
+        for (int w = 0; w < warp; w++) prev += s_wsum[w];
+        s_dstart[d] = prev + incl - run;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < RS_ITEMS; k++) {
+        if (dg[k] < 256) {
+            const uint32_t lp = s_dstart[dg[k]] + s_wcnt[warp][dg[k]] + rk[k];
+            s_key[lp] = key[k];
+            s_val[lp] = val[k];
+        }
+    }
+    __syncthreads();
+    const int cnt = (int)(n - t0 < RS_TILE ? n - t0 : RS_TILE);
+    for (int j = threadIdx.x; j < cnt; j += RS_NT) {
+        const uint64_t kk = s_key[j];
+        const int d = (int)((kk >> shift) & mask);
+        const uint64_t pos = s_gbase[d] + (uint64_t)(j - (int)s_dstart[d]);
+        kout[pos] = kk;
+        vout[pos] = s_val[j];
     }
 }
 

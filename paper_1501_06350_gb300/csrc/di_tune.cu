@@ -31,8 +31,17 @@ __global__ void k_shape(const Off *rp, int64_t n, unsigned long long *hubs, unsi
         if (deg > 256) h++;
         m = deg > m ? deg : m;
     }
-    if (h) atomicAdd(hubs, h);
-    atomicMax(maxdeg, m);
+    // one atomic of each kind per warp
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        h += __shfl_xor_sync(0xffffffffu, h, o);
+        const unsigned y = __shfl_xor_sync(0xffffffffu, m, o);
+        m = y > m ? y : m;
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (h) atomicAdd(hubs, h);
+        atomicMax(maxdeg, m);
+    }
 }
 
 static di_status shape_key(di_graph_s *g, double d, double tol, int precision, char *key, size_t cap,
