@@ -321,6 +321,21 @@ def batch_leg(torch, di, peak, reps=3, union=True):
     return out
 
 
+def aggregate_ranks(t_local: float, units: float, world: int, dist=None, device: str = "cuda"):
+    """Whole-job throughput over the ranks of a replicated run: the units all
+    ranks processed divided by the slowest rank's time.  Returns (value,
+    max time, total units)."""
+    if world <= 1:
+        return units / t_local, t_local, units
+    import torch
+    tt = torch.tensor([t_local], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    uu = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(uu)
+    t_max, total = float(tt.item()), float(uu.item())
+    return total / t_max, t_max, total
+
+
 def oracle_x(g, cp, ci):
     """The oracle's x to 1e-12 (|F|_1/(1-d)), to state each form's error."""
     import oracle
@@ -507,16 +522,7 @@ def main():
     solve_ms = [a.elapsed_time(b) for a, b, c in ev]
     pushes = sum(i1["edge_pushes"] + i2["edge_pushes"] + i3["edge_pushes"] for i1, i2, i3 in infos)
     t_local = sum(step_ms) / 1e3
-    t_max = t_local
-    pushes_all = pushes
-    if world > 1:
-        tt = torch.tensor([t_local], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-        pp = torch.tensor([pushes], dtype=torch.float64, device="cuda")
-        dist.all_reduce(pp)
-        pushes_all = float(pp.item())
-    value = pushes_all / t_max
+    value, t_max, pushes_all = aggregate_ranks(t_local, pushes, world, dist, "cuda")
 
     # roofline of the dominant kernel (push), CUDA events around each launch
     _, prof = st.solve(D, tol=TOL, profile=1, **sopt)
