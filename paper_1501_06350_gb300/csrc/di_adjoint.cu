@@ -140,7 +140,8 @@ di_status graph_build_reverse(di_graph_s *g, cudaStream_t s)
     r->nnz = m;
     r->weighted = true;
     Off *rp = nullptr;
-    DI_TRY(dalloc_t(&rp, n + 1, s));
+    DI_TRY(dalloc_t(&rp, n + 1 + RP_PAD, s));
+    DI_CUDA(cudaMemsetAsync(rp + n + 1, 0, sizeof(Off) * RP_PAD, s));
     r->rp = rp;
     DI_TRY(dalloc_t(&r->col, m, s));
     DI_TRY(dalloc_t(&r->w, m, s));

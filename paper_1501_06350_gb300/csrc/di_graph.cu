@@ -249,7 +249,8 @@ static di_status build(di_graph_s *g, int64_t n, int64_t nnz, const int64_t *ptr
     DI_TRY(t.get(&rows, m));
     DI_TRY(dalloc_t(&g->col, m, s));
     if (g->weighted) DI_TRY(dalloc_t(&g->w, m, s));
-    DI_TRY(dalloc_t(reinterpret_cast<uint32_t **>(&g->rp), n + 1, s));
+    DI_TRY(dalloc_t(reinterpret_cast<uint32_t **>(&g->rp), n + 1 + RP_PAD, s));
+    DI_CUDA(cudaMemsetAsync(static_cast<uint32_t *>(g->rp) + n + 1, 0, sizeof(uint32_t) * RP_PAD, s));
     k_compact<<<grid_for(nnz, 256), 256, 0, s>>>(keys, vals, keep, pos, nnz, w_d, wdt, g->col, rows,
                                                  g->w);
     count_launches(1);

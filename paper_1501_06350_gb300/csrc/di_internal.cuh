@@ -225,6 +225,10 @@ namespace di {
 constexpr int SEL_THREADS = 512;
 constexpr int SEL_PER_THREAD = 16;
 constexpr int TILE = SEL_THREADS * SEL_PER_THREAD;   // nodes per selection tile
+// Row-pointer arrays read by the push carry RP_PAD zeroed entries past rp[n]:
+// a lane whose four nodes include a selected one loads all five row pointers
+// of the four, which reaches rp[n + 3] in the last unit.
+constexpr int RP_PAD = 3;
 constexpr int PUSH_THREADS = 256;
 constexpr int HUB_DEG = 256;                         // default degree-bin threshold (di_opts.hub_deg)
 constexpr int PIECE = 1024;                          // default links per hub piece (di_opts.piece)

@@ -92,6 +92,14 @@ __device__ __forceinline__ double ldnc_f64(const double *a, unsigned long long p
     asm volatile("ld.global.nc.L2::cache_hint.b64 %0, [%1], %2;" : "=l"(r) : "l"(a), "l"(pol));
     return __longlong_as_double((long long)r);
 }
+__device__ __forceinline__ uint4 ldnc_u32x4(const unsigned *a, unsigned long long pol)
+{
+    uint4 r;
+    asm volatile("ld.global.nc.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+                 : "l"(a), "l"(pol));
+    return r;
+}
 __device__ __forceinline__ unsigned ldnc_u32(const unsigned *a, unsigned long long pol)
 {
     unsigned r;
@@ -862,6 +870,7 @@ __global__ void __launch_bounds__(PUSH_THREADS)
     const float *__restrict__ w32 = gp->w32;
     const int nhot = gp->nhot;
     constexpr int Q = 4;
+    static_assert(Q == 4, "the row pointers of a lane's nodes are one 16-byte load plus one");
     __shared__ unsigned long long s_links[PUSH_THREADS / 32];
     __shared__ unsigned long long s_hot[HOT_K];   // FP64: fixed point, units of 2^-hot_shift; FP32: floats
     // per warp, the current unit's 128 nodes: link offset of each node inside
@@ -923,8 +932,15 @@ __global__ void __launch_bounds__(PUSH_THREADS)
                     hb[k] = ld_b64(Hs + i0 + k, stream);
                     ds[k] = ldnc_f64(dscale + i0 + k, stream);
                 }
-#pragma unroll
-                for (int k = 0; k <= Q; k++) r[k] = ldnc_u32(rp + i0 + k, stream);
+                {
+                    // i0 is a multiple of 4: one 16-byte load for the first four
+                    const uint4 r4 = ldnc_u32x4(rp + i0, stream);
+                    r[0] = r4.x;
+                    r[1] = r4.y;
+                    r[2] = r4.z;
+                    r[3] = r4.w;
+                    r[4] = ldnc_u32(rp + i0 + Q, stream);
+                }
                 unsigned dg[Q];
 #pragma unroll
                 for (int k = 0; k < Q; k++) {
@@ -1105,6 +1121,8 @@ di_status state_set_bins(di_graph_s *g, di_state_s *st, int hub_deg, int piece, 
 di_status state_sync_ptrs(di_graph_s *g, di_state_s *st, cudaStream_t s)
 {
     GraphPtrs *h = st->host_gp;
+    // the push reads four row pointers at a time with a 16-byte load
+    if (reinterpret_cast<uintptr_t>(g->rp) % 16 != 0) return DI_ERR_CUDA;
     h->rp = static_cast<const Off *>(g->rp);
     h->pcol = g->pcol;
     h->w = g->w;

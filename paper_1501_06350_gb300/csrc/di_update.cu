@@ -414,7 +414,8 @@ di_status update_edges(di_graph_s *g, di_state_s *st, int64_t m, const int32_t *
     double *nwv = nullptr, *nwsum = nullptr;
     Off *nrp = nullptr;
     DI_TRY(dalloc_t(&ncol, mnew, s));
-    DI_TRY(dalloc_t(&nrp, n + 1, s));
+    DI_TRY(dalloc_t(&nrp, n + 1 + RP_PAD, s));
+    DI_CUDA(cudaMemsetAsync(nrp + n + 1, 0, sizeof(Off) * RP_PAD, s));
     if (g->weighted) {
         DI_TRY(dalloc_t(&nwv, mnew, s));
         DI_TRY(dalloc_t(&nwsum, n, s));
