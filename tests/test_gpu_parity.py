@@ -86,6 +86,44 @@ def test_graph_build_bit_exact(di, n, m, seed, weighted, layout):
     assert info["nnz"] == len(oi) and info["n_dangling"] == int((np.diff(op) == 0).sum())
 
 
+@pytest.mark.parametrize("layout", ["csr", "csc"])
+@pytest.mark.parametrize("weighted", [False, True])
+def test_graph_build_row_size_classes(di, layout, weighted):
+    """Rows of every length class the builder sorts differently (0, 1, up to 32,
+    up to 256, up to 8192 and longer links), with repeated targets and
+    self-loops, against the oracle's canonical CSR bit for bit."""
+    rng = np.random.default_rng(77)
+    n = 30_000
+    lens = [0, 1, 2, 31, 32, 33, 64, 65, 255, 256, 257, 1000, 8192, 8193, 20_000]
+    deg = np.zeros(n, dtype=np.int64)
+    rows = rng.choice(n, size=len(lens) * 3, replace=False)
+    for k, r in enumerate(rows):
+        deg[r] = lens[k % len(lens)]
+    rest = deg == 0
+    deg[rest] = rng.integers(0, 6, size=int(rest.sum()))
+    ptr = np.zeros(n + 1, dtype=np.int64)
+    ptr[1:] = np.cumsum(deg)
+    m = int(ptr[-1])
+    # targets from a small pool for some rows (many repeats), wide for others
+    idx = rng.integers(0, n, size=m).astype(np.int32)
+    for r in rows[::2]:
+        a, b = ptr[r], ptr[r + 1]
+        idx[a:b] = rng.integers(0, 50, size=b - a)
+        if b > a:
+            idx[a] = r                                  # a self-loop
+    w = rng.lognormal(0.0, 1.0, size=m).astype(np.float32) if weighted else None
+    if layout == "csc":
+        g = synth.to_csc(synth.RawGraph(n, ptr, idx, w, {}))
+        ptr, idx, w = g.ptr, g.idx, g.w
+    G = di.Graph(n, ptr, idx, w, layout=layout)
+    p, i, wo = G.export_csr()
+    op, oi, ow = oracle.canonical_csr(n, ptr, idx, w, 0 if layout == "csr" else 1)
+    assert np.array_equal(_np(p), op)
+    assert np.array_equal(_np(i), oi)
+    if weighted:
+        assert np.array_equal(_np(wo), ow)
+
+
 def test_graph_build_from_device_buffers(di):
     g = pa10k()
     G = di.Graph(g.n, torch.from_numpy(g.ptr).cuda(), torch.from_numpy(g.idx).cuda())
