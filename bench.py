@@ -366,14 +366,19 @@ def traffic_for(record: str, opts: dict | None = None):
     return rec.get("dram_bytes_per_launch")
 
 
-def forms(st, G, g, torch, x_ref, reps=5):
+def forms(st, G, g, torch, x_ref, di, reps=5):
     """Time to tol of a from-scratch solve in each form (L2 flushed before each
     run, CUDA events inside the library), with the L1 error of the returned H
-    against the FP64 oracle's x when it is available."""
+    against the FP64 oracle's x when it is available; each form at the library
+    defaults and at the options the autotuner picks for its precision."""
     from paper_1501_06350_gb300 import _lib
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     out = {}
-    for name, kw in (("f64", {}), ("f32_refined", {"precision": _lib.DI_PREC_F32})):
+    runs = [("f64", {}), ("f32_refined", {"precision": _lib.DI_PREC_F32})]
+    for name, prec in (("f64_tuned", _lib.DI_PREC_F64), ("f32_refined_tuned", _lib.DI_PREC_F32)):
+        tuned, _ = di.autotune(G, D, TOL, prec, 20)
+        runs.append((name, dict(tuned)))
+    for name, kw in runs:
         ts, info, H = [], None, None
         for _ in range(reps):
             flush.zero_()
@@ -385,8 +390,11 @@ def forms(st, G, g, torch, x_ref, reps=5):
                "refine_links": info["refine_links"], "resid_l1": info["resid_l1"], "bound": info["bound"]}
         if x_ref is not None:
             rec["err_l1_vs_oracle"] = float(np.abs(H.cpu().numpy() - x_ref).sum())
+        if name.endswith("_tuned"):
+            rec["options"] = {k: kw[k] for k in ("theta_factor", "hub_deg", "piece", "refine_ratio") if k in kw}
         out[name] = rec
     out["f32_speedup"] = out["f64"]["time_to_tol_ms"] / out["f32_refined"]["time_to_tol_ms"]
+    out["f32_speedup_tuned"] = out["f64_tuned"]["time_to_tol_ms"] / out["f32_refined_tuned"]["time_to_tol_ms"]
     return out
 
 
@@ -577,7 +585,7 @@ def main():
         out["cpu_baseline"] = cpu_baseline(g, cp, ci)
         x_ref = oracle_x(g, cp, ci)
     if rank == 0 and not args.no_forms:
-        out["forms"] = forms(st, G, g, torch, x_ref)
+        out["forms"] = forms(st, G, g, torch, x_ref, di)
     if rank == 0 and (not args.no_adjoint or not args.no_batch):
         st.close()
         G.close()
