@@ -66,36 +66,17 @@ __global__ void k_scale_into(double *out, const double *in, int64_t n, double a)
         out[i] = a * in[i];
 }
 
-// dL/dw per link of the out-CSR, in its order.  One warp per 32 consecutive
-// links: lanes 0 and 1 find the rows of the first and last link by binary
-// search over the row pointers, then every lane searches its own row inside
-// that (short) range.
-__global__ void k_grad_w(const Off *rp, const int32_t *col, const double *wsum, int64_t n, int64_t nnz,
-                         const double *x, const double *lam, const double *F, const double *g, double d,
+// dL/dw per link of the out-CSR, in its order, one thread per link: the row
+// j of link e is the largest j with rp[j] <= e, searched between the rows of
+// the bucket starts around e (tab, see row_bucket_table).
+__global__ void k_grad_w(const Off *rp, const uint32_t *tab, const int32_t *col, const double *wsum, int64_t n,
+                         int64_t nnz, const double *x, const double *lam, const double *F, const double *g, double d,
                          double *grad)
 {
-    const int lane = threadIdx.x & 31;
-    const int64_t nchunks = (nnz + 31) / 32;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < nchunks; c += nw) {
-        const int64_t e0 = c * 32;
-        const int64_t last = e0 + 31 < nnz ? e0 + 31 : nnz - 1;
-        int64_t jr = 0;
-        if (lane < 2) {
-            // largest j in [0, n) with rp[j] <= target (that row holds the link)
-            const Off target = (Off)(lane == 0 ? e0 : last);
-            int64_t lo = 0, hi = n - 1;
-            while (lo < hi) {
-                const int64_t mid = (lo + hi + 1) >> 1;
-                if (__ldg(rp + mid) <= target) lo = mid;
-                else hi = mid - 1;
-            }
-            jr = lo;
-        }
-        const int64_t jf = __shfl_sync(0xffffffffu, jr, 0), jl = __shfl_sync(0xffffffffu, jr, 1);
-        const int64_t e = e0 + lane;
-        if (e >= nnz) continue;
-        int64_t lo = jf, hi = jl;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t q = e >> KEY_BUCKET_SHIFT;
+        int64_t lo = __ldg(tab + q), hi = __ldg(tab + q + 1);   // rp[lo] <= e, row(e) <= hi
         while (lo < hi) {
             const int64_t mid = (lo + hi + 1) >> 1;
             if (__ldg(rp + mid) <= (Off)e) lo = mid;
@@ -184,10 +165,18 @@ di_status adjoint(di_graph_s *g, double d, const double *gvec, const double *x, 
         count_launches(1);
     }
     if (grad_w && g->nnz) {
-        k_grad_w<<<grid_for(g->nnz, 256), 256, 0, s>>>(static_cast<const Off *>(g->rp), g->col,
-                                                       g->weighted ? g->wsum : nullptr, n, g->nnz, x, st->H,
-                                                       st->F, gvec, d, grad_w);
-        count_launches(1);
+        const int64_t nbk = (g->nnz + (1 << KEY_BUCKET_SHIFT) - 1) >> KEY_BUCKET_SHIFT;
+        uint32_t *tab = nullptr;
+        DI_TRY(dalloc_t(&tab, nbk + 1, s));
+        di_status rt = row_bucket_table(static_cast<const Off *>(g->rp), n, g->nnz, tab, s);
+        if (rt == DI_OK) {
+            k_grad_w<<<grid_for(g->nnz, 256), 256, 0, s>>>(static_cast<const Off *>(g->rp), tab, g->col,
+                                                           g->weighted ? g->wsum : nullptr, n, g->nnz, x, st->H,
+                                                           st->F, gvec, d, grad_w);
+            count_launches(1);
+        }
+        dfree(tab, s);
+        DI_TRY(rt);
     }
     DI_CUDA(cudaGetLastError());
     DI_CUDA(cudaStreamSynchronize(s));

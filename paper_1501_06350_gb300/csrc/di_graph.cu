@@ -37,11 +37,11 @@ __global__ void k_validate(const int64_t *ptr, const int32_t *idx, const void *w
     if (e) atomicOr(err, e);
 }
 
-// Row lookup table for the link-parallel key construction: tab[q] is the row
-// holding link q * 2^KEY_BUCKET_SHIFT (each such link lies in exactly one
-// non-empty row, which writes it); tab[nbk] = n - 1.
-constexpr int KEY_BUCKET_SHIFT = 8;
-__global__ void k_bucket_rows(const int64_t *ptr, int64_t n, int64_t nbk, uint32_t *tab)
+// Row lookup table for link-parallel kernels: tab[q] is the row holding link
+// q * 2^KEY_BUCKET_SHIFT (each such link lies in exactly one non-empty row,
+// which writes it); tab[nbk] = n - 1.
+template <typename P>
+__global__ void k_bucket_rows(const P *ptr, int64_t n, int64_t nbk, uint32_t *tab)
 {
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n;
          r += (int64_t)gridDim.x * blockDim.x) {
@@ -194,6 +194,15 @@ static unsigned grid_for(int64_t work, int threads)
     return (unsigned)b;
 }
 
+di_status row_bucket_table(const uint32_t *rp, int64_t n, int64_t nnz, uint32_t *tab, cudaStream_t s)
+{
+    const int64_t nbk = (nnz + (1 << KEY_BUCKET_SHIFT) - 1) >> KEY_BUCKET_SHIFT;
+    k_bucket_rows<uint32_t><<<grid_for(n, 256), 256, 0, s>>>(rp, n, nbk, tab);
+    count_launches(1);
+    DI_CUDA(cudaGetLastError());
+    return DI_OK;
+}
+
 static di_status build(di_graph_s *g, int64_t n, int64_t nnz, const int64_t *ptr_d,
                        const int32_t *idx_d, const void *w_d, int wdt, int layout, cudaStream_t s)
 {
@@ -221,7 +230,7 @@ static di_status build(di_graph_s *g, int64_t n, int64_t nnz, const int64_t *ptr
         const int64_t nbk = (nnz + (1 << KEY_BUCKET_SHIFT) - 1) >> KEY_BUCKET_SHIFT;
         uint32_t *tab;
         DI_TRY(t.get(&tab, nbk + 1));
-        k_bucket_rows<<<grid_for(n, 256), 256, 0, s>>>(ptr_d, n, nbk, tab);
+        k_bucket_rows<int64_t><<<grid_for(n, 256), 256, 0, s>>>(ptr_d, n, nbk, tab);
         k_make_keys<<<grid_for(nnz, 256), 256, 0, s>>>(ptr_d, idx_d, n, nnz, layout, tab, keys, vals);
         count_launches(2);
         DI_CUDA(cudaGetLastError());

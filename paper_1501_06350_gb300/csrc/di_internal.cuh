@@ -28,7 +28,10 @@ di_status note_cuda(cudaError_t e);          // records e for di_last_cuda_error
 // Stream-ordered device allocation; returns DI_ERR_OOM on failure.
 di_status dalloc(void **p, size_t bytes, cudaStream_t s);
 void dfree(void *p, cudaStream_t s);
-void pool_keep(int device);   // keep freed scratch in the default pool (once per device)
+void pool_keep(int device);
+// tab[q] = row of link q << KEY_BUCKET_SHIFT for q < ceil(nnz / 2^KEY_BUCKET_SHIFT);
+// tab[that count] = n - 1.  tab holds that count + 1 entries; nnz >= 1.
+di_status row_bucket_table(const uint32_t *rp, int64_t n, int64_t nnz, uint32_t *tab, cudaStream_t s);   // keep freed scratch in the default pool (once per device)
 
 template <typename T>
 di_status dalloc_t(T **p, size_t count, cudaStream_t s)
@@ -229,6 +232,8 @@ constexpr int TILE = SEL_THREADS * SEL_PER_THREAD;   // nodes per selection tile
 // a lane whose four nodes include a selected one loads all five row pointers
 // of the four, which reaches rp[n + 3] in the last unit.
 constexpr int RP_PAD = 3;
+// Links per bucket of the row lookup table (row_bucket_table).
+constexpr int KEY_BUCKET_SHIFT = 8;
 constexpr int PUSH_THREADS = 256;
 constexpr int HUB_DEG = 256;                         // default degree-bin threshold (di_opts.hub_deg)
 constexpr int PIECE = 1024;                          // default links per hub piece (di_opts.piece)
