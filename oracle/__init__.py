@@ -9,7 +9,11 @@ helpers below are plain NumPy/LAPACK restatements of the paper's definitions.
 Parity status: every routine is pinned by ``tests/test_oracle_*.py`` against
 closed forms, brute force, the dense direct solution (Section 2.1, the closed
 form x = (1-d)(I-dP)^-1 Z), the invariant Eq. HnFn and the bounds of
-Theorems 1-3; none is "parity unpinned".
+Theorems 1-3; the Section 3.3 helpers (``completed_solution``,
+``dangling_loss``) by exact rational solves of the completed matrix, the
+rank-one closed form of a graph without links, the paper's normalisation
+factor and the mass balance (``tests/test_oracle_completion.py``).  None is
+"parity unpinned".
 """
 from __future__ import annotations
 
