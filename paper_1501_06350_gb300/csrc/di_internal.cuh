@@ -108,6 +108,7 @@ struct di_graph_s {
     float *w32 = nullptr;     // [nnz] FP32 copy of w for the FP32-fluid push (weighted only)
     unsigned *indeg = nullptr;    // [n] in-links per page, kept current by updates
     int32_t *hot_node = nullptr;  // [HOT_K] page of each hot slot
+    int *slot_of = nullptr;       // [n] hot slot of each page, -1 if none (kept across link updates)
     int nhot = 0;
     int64_t pcol_version = -1;
     // reverse graph (links i -> j for every j -> i, weight P[i][j]) and the
@@ -146,7 +147,7 @@ struct DevCtl {
     int inf_norm;              // 1: stop test and threshold cap on max |F_i| (adjoint)
     unsigned int done;         // 0 running, 1 converged, 2 sweep cap
     unsigned int ticket2;      // last-block ticket of the reductions
-    unsigned int err;          // reserved for device-side error flags
+    unsigned int err;          // unused (keeps the layout of the block)
     unsigned int push_ready;   // 1: the mask/pieces describe a frontier not yet pushed
     unsigned int pad1;
 };
@@ -187,6 +188,7 @@ struct di_state_s {
     DevCtl *rctl = nullptr;
     DevCtl *host_rctl = nullptr;
     double *dscale = nullptr;      // d / W_j (or d / out(j)) per node, 0 if dangling
+    double *dtab = nullptr;        // d / k for k <= DTAB_MAX (fills dscale without FP64 divisions)
     double dscale_d = -1.0;        // damping dscale was built for
     // frontier of the last selection: one bit per selected node that is not a
     // hub; selected hubs (more than hub_deg links) go to hub_list
@@ -236,6 +238,7 @@ constexpr int RP_PAD = 3;
 constexpr int KEY_BUCKET_SHIFT = 8;
 constexpr int PUSH_THREADS = 256;
 constexpr int HUB_DEG = 256;                         // default degree-bin threshold (di_opts.hub_deg)
+constexpr int DTAB_MAX = 65536;                      // out-degrees with a tabulated d / out(j)
 constexpr int PIECE = 1024;                          // default links per hub piece (di_opts.piece)
 constexpr int RED_THREADS = 256;
 constexpr int STAT_CAP = 4096;                       // sweeps with recorded statistics

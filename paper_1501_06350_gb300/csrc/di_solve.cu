@@ -220,13 +220,29 @@ __global__ void k_init(double *F, double *H, const double *Z, int64_t n, double 
 
 // d / W_j (weighted) or d / out(j): the factor turning taken fluid into the
 // per-unit-weight share pushed along column j of P (Eq. def-p).
-__global__ void k_dscale(const Off *rp, const double *wsum, int64_t n, double d, double *dscale)
+// Unweighted rows read d / out(j) from the table of k_dtab when given (FP64
+// division is slow on this part; the table holds the same quotients).
+__global__ void k_dscale(const Off *rp, const double *wsum, const double *dtab, int64_t n, double d,
+                         double *dscale)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const Off deg = rp[i + 1] - rp[i];
-        dscale[i] = deg == 0 ? 0.0 : (wsum ? d / wsum[i] : d / (double)deg);
+        double v;
+        if (deg == 0) v = 0.0;
+        else if (wsum) v = d / wsum[i];
+        else if (dtab && deg <= (Off)DTAB_MAX) v = __ldg(dtab + deg);
+        else v = d / (double)deg;
+        dscale[i] = v;
     }
+}
+
+// d / k for k = 0 .. DTAB_MAX (0 at k = 0): the same division as k_dscale,
+// so a row's share from the table is bit for bit its d / out(j).
+__global__ void k_dtab(double d, double *dtab)
+{
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k <= DTAB_MAX; k += gridDim.x * blockDim.x)
+        dtab[k] = k == 0 ? 0.0 : d / (double)k;
 }
 
 __global__ void k_scale(double *out, const double *in, int64_t n, double a)
@@ -662,12 +678,21 @@ __global__ void __launch_bounds__(SEL_THREADS)
             if (stats && sweep >= 1 && sweep <= (unsigned long long)STAT_CAP) stats[2 * (sweep - 1)] = links;
             vc->sweep_links = 0;
             vc->l1 = sa;
-            // what one sweep can add into one page: at most the whole pushed
-            // volume d |F|_1 / (1 - d) < 8 |F|_1 (d <= 7/8) in the plain solve;
-            // on the reverse graph a page j receives d f_i P[i][j] from its
-            // out-neighbours i and the column of P sums to 1, so at most about
-            // d max |F| per take: 8 max |F| leaves a wide margin
-            vc->hot_scale = inf_norm ? 8.0 * (double)__uint_as_float((unsigned)mu) : sa;
+            // hot_scale >= V / 8, V a bound on what one sweep adds into one
+            // page (the push keeps 8 hot_scale of headroom per page).  Plain
+            // solve: a unit of fluid can be taken again after each hop inside
+            // one sweep, keeping d of it per hop, so the fluid taken in one
+            // sweep is at most |F|_1 / (1 - d) and V = d |F|_1 / (1 - d).
+            // Reverse graph (infinity norm): a page j receives d f_i P[i][j]
+            // from the pages i that link to it in the reverse graph, and the
+            // column sums of P are at most 1, so no page ever holds more than
+            // max |F| / (1 - d) during the sweep and V = d max |F| / (1 - d).
+            // (The refinement pass takes each node once: V = d |D|_1 < sa.)
+            {
+                const double hop = vc->d / (1.0 - vc->d);
+                const double base = inf_norm ? (double)__uint_as_float((unsigned)mu) : sa;
+                vc->hot_scale = base * fmax(inf_norm ? 8.0 : 1.0, 0.125 * hop);
+            }
             if (!done) {
                 vc->diffusions = vc->diffusions + sd;
                 vc->nent = sc;
@@ -787,13 +812,21 @@ __device__ __forceinline__ float link_weight(const float *w32, Off link, unsigne
 // Shared-memory accumulation for the hot pages: FP64 contributions as 64-bit
 // fixed point (native integer atomics; the shared FP64 add is not native),
 // FP32 contributions with the native shared FP32 add.
-__device__ __forceinline__ void hot_add(unsigned long long *s_hot, int slot, double v, int hot_shift)
+// Returns false (nothing added) for a contribution too large for the fixed
+// point, |v| 2^hot_shift >= 2^59; the caller then adds it in global memory.
+// (hot_scale bounds every sweep so that this does not happen; the check keeps
+// a contribution from ever being converted out of range.)
+__device__ __forceinline__ bool hot_add(unsigned long long *s_hot, int slot, double v, int hot_shift)
 {
+    const int ex = (int)(((unsigned long long)__double_as_longlong(v) >> 52) & 0x7ffu);
+    if (ex - 1023 + hot_shift > 58) return false;
     atomicAdd(s_hot + slot, (unsigned long long)to_fixed64(v, hot_shift));
+    return true;
 }
-__device__ __forceinline__ void hot_add(unsigned long long *s_hot, int slot, float v, int)
+__device__ __forceinline__ bool hot_add(unsigned long long *s_hot, int slot, float v, int)
 {
     atomicAdd(reinterpret_cast<float *>(s_hot) + slot, v);
+    return true;
 }
 __device__ __forceinline__ void hot_flush(double *Fd, const int32_t *hot_node, const unsigned long long *s_hot,
                                           int k, int hot_shift, unsigned long long keep)
@@ -814,8 +847,8 @@ __device__ __forceinline__ void hot_flush(float *Fd, const int32_t *hot_node, co
 template <typename T, bool WEIGHTED, typename LinkOf>
 __device__ __forceinline__ void scatter_links(unsigned total, LinkOf lane_link, const int32_t *pcol,
                                               const double *w, const float *w32, T *Fd,
-                                              unsigned long long *s_hot, int hot_shift, unsigned long long keep,
-                                              unsigned long long stream)
+                                              unsigned long long *s_hot, const int32_t *hot_node, int hot_shift,
+                                              unsigned long long keep, unsigned long long stream)
 {
     const int lane = threadIdx.x & 31;
     for (unsigned base = 0; base < total; base += 128) {
@@ -843,7 +876,8 @@ __device__ __forceinline__ void scatter_links(unsigned total, LinkOf lane_link, 
         for (int g = 0; g < 4; g++) {
             if (!ok[g]) continue;
             if (c[g] >= 0) red_add(Fd + c[g], v[g], keep);
-            else hot_add(s_hot, c[g] & 0x7fffffff, v[g], hot_shift);
+            else if (!hot_add(s_hot, c[g] & 0x7fffffff, v[g], hot_shift))
+                red_add(Fd + __ldg(hot_node + (c[g] & 0x7fffffff)), v[g], keep);
         }
     }
 }
@@ -851,12 +885,14 @@ __device__ __forceinline__ void scatter_links(unsigned total, LinkOf lane_link, 
 // Warp-centric take and push.  Work unit u < nunits: the 128 nodes
 // [128u, 128u + 128), lane l owning nodes 128u + 4l .. 4l + 3 and their bits
 // of mask words 4u .. 4u + 3; u >= nunits: hub piece u - nunits.  All takes
-// and loads of a unit are issued before any is used.  The taken nodes' links
-// are enumerated 32 at a time; a link finds its lane by a binary search over
-// the lanes' exclusive link prefixes (shuffles) and its node among the lane's
-// four by their running degrees.  Ft / Fd / Hs / SUB as for k_plan.
+// and loads of a unit are issued before any is used; the history gets the
+// taken fluid by a reduction (no load: a node is taken by one warp per
+// sweep, and the add needs nothing back).  The taken nodes' links are dealt
+// to the lanes 128 at a time; a link finds its node by a binary search over
+// the unit's link offsets in shared memory.  Ft / Fd / Hs / SUB as for
+// k_plan.  At most 64 registers: four CTAs of 256 threads per SM.
 template <typename T, bool WEIGHTED, bool SUB>
-__global__ void __launch_bounds__(PUSH_THREADS)
+__global__ void __launch_bounds__(PUSH_THREADS, 4)
     k_push(T *Ft, T *Fd, double *Hs, const GraphPtrs *__restrict__ gp, const double *__restrict__ dscale,
            const unsigned *__restrict__ mask, int64_t ngroups, const int32_t *__restrict__ hot_node, DevCtl *ctl)
 {
@@ -880,11 +916,9 @@ __global__ void __launch_bounds__(PUSH_THREADS)
     __shared__ T s_val[PUSH_THREADS / 32][32 * 4];
     volatile DevCtl *vc = ctl;
     if (!vc->push_ready) return;
-    // hot_scale bounds what this sweep adds into one page (see k_plan; fluid
-    // taken twice in one sweep counts twice, and for d > 7/8 the share of any
-    // one CTA stays far below the bound): with 2^(e-1) <= hot_scale < 2^e,
-    // units of 2^(e - 58) keep every slot below 2^61.  (The refinement pass
-    // takes each node once: its pushes add up to at most d |D|_1 < |D|_1.)
+    // 8 hot_scale bounds what this sweep adds into one page, for every d
+    // (k_plan derives it): with 2^(e-1) <= hot_scale < 2^e, units of
+    // 2^(e - 58) keep every slot below 2^61.
     int e = 0;
     frexp(vc->hot_scale, &e);
     const int hot_shift = 58 - e;
@@ -919,17 +953,14 @@ __global__ void __launch_bounds__(PUSH_THREADS)
             unsigned c1 = 0, c2 = 0, c3 = 0, tot = 0;
             if (bits) {
                 U fb[Q];
-                unsigned long long hb[Q];
                 double ds[Q];
 #pragma unroll
                 for (int k = 0; k < Q; k++) {
                     fb[k] = 0;
-                    hb[k] = 0ull;
                     ds[k] = 0.0;
                     if (!((bits >> k) & 1u)) continue;
                     // take (Eq. defF): whatever fluid the node holds now
                     fb[k] = atom_exch_word(Ft + i0 + k, keep);
-                    hb[k] = ld_b64(Hs + i0 + k, stream);
                     ds[k] = ldnc_f64(dscale + i0 + k, stream);
                 }
                 {
@@ -948,9 +979,7 @@ __global__ void __launch_bounds__(PUSH_THREADS)
                     val[k] = (T)0;
                     if (!((bits >> k) & 1u)) continue;
                     const double f = (double)word_val(fb[k]);
-                    st_b64(Hs + i0 + k,
-                           (unsigned long long)__double_as_longlong(__longlong_as_double((long long)hb[k]) + f),
-                           stream);
+                    red_add_f64(Hs + i0 + k, f, stream);
                     if (SUB) red_add_f64(reinterpret_cast<double *>(Fd) + i0 + k, -f, keep);
                     dg[k] = r[k + 1] - r[k];
                     val[k] = (T)(f * ds[k]);
@@ -976,8 +1005,7 @@ __global__ void __launch_bounds__(PUSH_THREADS)
             links += total;
             // park the unit's nodes in shared memory: a link then finds its
             // node by a binary search over the 128 starts (shared loads, the
-            // lanes of a batch mostly read the same entries) instead of a
-            // search plus a dozen shuffles
+            // lanes of a batch mostly read the same entries)
             const int wq = threadIdx.x >> 5;
             __syncwarp();
             s_start[wq][Q * lane] = excl;
@@ -998,7 +1026,7 @@ __global__ void __launch_bounds__(PUSH_THREADS)
                 link = s_row[wq][k] + (e - s_start[wq][k]);
                 vj = s_val[wq][k];
             };
-            scatter_links<T, WEIGHTED>(total, lane_link, pcol, w, w32, Fd, s_hot, hot_shift, keep, stream);
+            scatter_links<T, WEIGHTED>(total, lane_link, pcol, w, w32, Fd, s_hot, hot_node, hot_shift, keep, stream);
         } else {
             const unsigned p = u - nunits;
             const Off row = ldnc_u32(pc_row + p, stream), len = ldnc_u32(pc_len + p, stream);
@@ -1008,7 +1036,7 @@ __global__ void __launch_bounds__(PUSH_THREADS)
                 link = row + e;
                 vj = pv;
             };
-            scatter_links<T, WEIGHTED>(len, piece_link, pcol, w, w32, Fd, s_hot, hot_shift, keep, stream);
+            scatter_links<T, WEIGHTED>(len, piece_link, pcol, w, w32, Fd, s_hot, hot_node, hot_shift, keep, stream);
         }
     }
     if (lane == 0) s_links[threadIdx.x >> 5] = links;
@@ -1023,19 +1051,19 @@ __global__ void __launch_bounds__(PUSH_THREADS)
 }
 
 // Static hub bit mask: node i has more than hub_deg out-links.
+// One node per thread, one word per warp (ballot); the grid covers whole words.
 __global__ void k_hubbits(const Off *rp, int64_t n, int64_t words, Off hub_deg, unsigned *hubbits,
                           unsigned long long *count)
 {
     unsigned long long c = 0;
-    for (int64_t wi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; wi < words;
-         wi += (int64_t)gridDim.x * blockDim.x) {
-        unsigned word = 0;
-        for (int b = 0; b < 32; b++) {
-            const int64_t i = wi * 32 + b;
-            if (i < n && rp[i + 1] - rp[i] > hub_deg) word |= 1u << b;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < words * 32;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const bool hub = i < n && rp[i + 1] - rp[i] > hub_deg;
+        const unsigned word = __ballot_sync(0xffffffffu, hub);
+        if ((threadIdx.x & 31) == 0) {
+            hubbits[i >> 5] = word;
+            c += __popc(word);
         }
-        hubbits[wi] = word;
-        c += __popc(word);
     }
     if (c) atomicAdd(count, c);
 }
@@ -1079,7 +1107,7 @@ di_status state_prepare_graph(di_graph_s *g, di_state_s *st, cudaStream_t s)
     unsigned long long *cnt;
     DI_TRY(t.get(&cnt, 1));
     DI_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), s));
-    k_hubbits<<<grid_for(words, 256), 256, 0, s>>>(static_cast<const Off *>(g->rp), g->n, words,
+    k_hubbits<<<grid_for(words * 32, 256), 256, 0, s>>>(static_cast<const Off *>(g->rp), g->n, words,
                                                    (Off)st->hub_deg, st->hubbits, cnt);
     count_launches(1);
     DI_CUDA(cudaGetLastError());
@@ -1146,6 +1174,7 @@ di_status state_alloc(di_state_s *st, cudaStream_t s)
     DI_TRY(dalloc_t(&st->F, slots, s));
     DI_TRY(dalloc_t(&st->H, slots, s));
     DI_TRY(dalloc_t(&st->dscale, n, s));
+    DI_TRY(dalloc_t(&st->dtab, DTAB_MAX + 1, s));
     DI_TRY(dalloc_t(&st->mask, slots / 32, s));
     DI_TRY(dalloc_t(&st->hubbits, slots / 32, s));
     DI_TRY(dalloc_t(&st->tile_cnt, st->ntiles, s));
@@ -1180,7 +1209,7 @@ di_status state_free(di_state_s *st)
     if (st->gexec) cudaGraphExecDestroy(st->gexec);
     if (st->gexec32) cudaGraphExecDestroy(st->gexec32);
     if (st->gstream) cudaStreamDestroy(st->gstream);
-    void *bufs[] = {st->F, st->H, st->dscale, st->mask, st->hubbits, st->hub_list, st->pc_row, st->pc_len,
+    void *bufs[] = {st->F, st->H, st->dscale, st->dtab, st->mask, st->hubbits, st->hub_list, st->pc_row, st->pc_len,
                     st->pc_val, st->tile_cnt, st->tile_diff, st->tile_l1f, st->tile_maxf, st->tile_l1,
                     st->tile_l, st->ctl, st->stats, st->F32, st->D, st->rctl, st->tile_maxu, st->tile_max,
                     st->gp};
@@ -1444,9 +1473,10 @@ di_status solve_loop(di_graph_s *g, di_state_s *st, double tol, const di_opts *o
         count_launches(1);
     }
     if (st->dscale_d != d) {
-        k_dscale<<<grid_for(n, 256), 256, 0, s>>>(static_cast<const Off *>(g->rp), g->wsum, n, d,
+        k_dtab<<<grid_for(DTAB_MAX + 1, 256), 256, 0, s>>>(d, st->dtab);
+        k_dscale<<<grid_for(n, 256), 256, 0, s>>>(static_cast<const Off *>(g->rp), g->wsum, st->dtab, n, d,
                                                   st->dscale);
-        count_launches(1);
+        count_launches(2);
         st->dscale_d = d;
     }
     DevCtl *hc = st->host_ctl;
@@ -1543,7 +1573,6 @@ di_status solve_loop(di_graph_s *g, di_state_s *st, double tol, const di_opts *o
         info->resid_inf = hc->final_max;
         if (inf_norm) info->bound = hc->final_max / (1.0 - d);
     }
-    if (hc->err) return DI_ERR_DEVICE_TIMEOUT;
     if (hc->done == 2) return DI_ERR_NOT_CONVERGED;
     if (hc->done != 1) return DI_ERR_CUDA;
     return DI_OK;
@@ -1646,7 +1675,7 @@ di_status select_only(di_graph_s *g, const double *F, double theta, int32_t *ids
             cudaMemcpyAsync(st.ctl, hc, sizeof(DevCtl), cudaMemcpyHostToDevice, s);
             cudaMemcpyAsync(st.F, F, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
             state_sync_ptrs(g, &st, s);
-            k_dscale<<<grid_for(n, 256), 256, 0, s>>>(static_cast<const Off *>(g->rp), g->wsum, n, 0.85,
+            k_dscale<<<grid_for(n, 256), 256, 0, s>>>(static_cast<const Off *>(g->rp), g->wsum, nullptr, n, 0.85,
                                                       st.dscale);
             count_launches(1);
             launch_select(g, &st, sweep_of(&st, SW_F64), s, 0, cudaGraphConditionalHandle{}, sel_ids);

@@ -252,6 +252,30 @@ def small_graph(n: int, m: int, seed_offset: int, dangling_frac: float = 0.1,
     return RawGraph(n, ptr, dst.astype(np.int32), w, dict(kind="small", n=n))
 
 
+def with_in_hubs(g: RawGraph, n_hubs: int, frac: float, seed_offset: int) -> RawGraph:
+    """The same links plus ``n_hubs`` heavy in-hubs: each page that already has
+    out-links gets, with probability ``frac``, one extra link to a hub chosen
+    uniformly (hubs are the pages 0 .. n_hubs-1).  Rows keep input order with
+    the extra link appended, so duplicates and self-links may appear."""
+    rng = rng_for(8000 + seed_offset)
+    deg = np.diff(g.ptr)
+    extra = (rng.random(g.n) < frac) & (deg > 0)
+    hub = rng.integers(0, n_hubs, size=g.n)
+    ptr = np.zeros(g.n + 1, dtype=np.int64)
+    ptr[1:] = np.cumsum(deg + extra)
+    idx = np.empty(int(ptr[-1]), dtype=np.int32)
+    w = None if g.w is None else np.empty(int(ptr[-1]), dtype=g.w.dtype)
+    src = np.repeat(np.arange(g.n, dtype=np.int64), deg)
+    pos = ptr[src] + (np.arange(g.nnz, dtype=np.int64) - g.ptr[src])
+    idx[pos] = g.idx
+    rows = np.nonzero(extra)[0]
+    idx[ptr[rows + 1] - 1] = hub[rows]
+    if w is not None:
+        w[pos] = g.w
+        w[ptr[rows + 1] - 1] = rng.lognormal(0.0, 1.0, size=len(rows)).astype(g.w.dtype)
+    return RawGraph(g.n, ptr, idx, w, dict(g.meta, in_hubs=n_hubs, hub_frac=frac))
+
+
 def edges_from_csr(g: RawGraph) -> tuple[np.ndarray, np.ndarray]:
     """Expand a CSR into (src, dst) arrays in input order."""
     src = np.repeat(np.arange(g.n, dtype=np.int64), np.diff(g.ptr))
