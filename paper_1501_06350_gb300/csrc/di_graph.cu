@@ -412,9 +412,9 @@ di_status graph_build_push_targets(di_graph_s *g, cudaStream_t s)
     Temps t(s);
     unsigned *nhot;
     unsigned long long *hist;
-    int *slot_of;
+    if (!g->slot_of) DI_TRY(dalloc_t(&g->slot_of, n, s));
+    int *slot_of = g->slot_of;
     DI_TRY(t.get(&hist, 130));
-    DI_TRY(t.get(&slot_of, n));
     DI_TRY(t.get(&nhot, 1));
     DI_CUDA(cudaMemsetAsync(hist, 0, sizeof(unsigned long long) * 130, s));
     DI_CUDA(cudaMemsetAsync(nhot, 0, sizeof(unsigned), s));
@@ -527,8 +527,10 @@ void graph_release(di_graph_s *g)
     dfree(g->pcol, s);
     dfree(g->w32, s);
     dfree(g->hot_node, s);
+    dfree(g->slot_of, s);
     dfree(g->indeg, s);
     cudaStreamSynchronize(s);
+    g->slot_of = nullptr;
     g->pcol = nullptr;
     g->w32 = nullptr;
     g->hot_node = nullptr;

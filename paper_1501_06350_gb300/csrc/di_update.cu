@@ -69,10 +69,11 @@ __global__ void k_unique(const uint64_t *keys, const uint32_t *vals, const uint8
 
 // Classify each distinct batch link against its old row (binary search);
 // count the row's degree change, flag the row, keep in-degrees current.
-__global__ void k_classify(const uint64_t *ukey, const int8_t *uop, const double *uw, int64_t nu, const Off *rp,
-                           const int32_t *col, const double *w, uint8_t *eff, int *delta, uint8_t *touched,
-                           unsigned *indeg)
+__global__ void k_classify(const uint64_t *ukey, const int8_t *uop, const double *uw, const uint64_t *nu_dev,
+                           const Off *rp, const int32_t *col, const double *w, uint8_t *eff, int *delta,
+                           uint8_t *touched, unsigned *indeg)
 {
+    const int64_t nu = (int64_t)*nu_dev;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nu;
          k += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t sr = (uint32_t)(ukey[k] >> 32);
@@ -123,7 +124,8 @@ __global__ void k_rp_from_scan(const uint64_t *ex, const uint64_t *total, int64_
 // Rows without an effective change keep their links; a warp moves the links
 // of 32 consecutive rows (lane l owns row 32g + l) to their new offsets.
 __global__ void k_copy_rows(const Off *rp, const Off *nrp, const int32_t *col, const double *w,
-                            const uint8_t *touched, int64_t n, int32_t *ncol, double *nw)
+                            const int32_t *pcol, const uint8_t *touched, int64_t n, int32_t *ncol, double *nw,
+                            int32_t *npcol)
 {
     const int lane = threadIdx.x & 31;
     const int64_t ngroups = (n + 31) / 32;
@@ -158,6 +160,7 @@ __global__ void k_copy_rows(const Off *rp, const Off *nrp, const int32_t *col, c
             if (e < total) {
                 ncol[to] = col[from];
                 if (w) nw[to] = w[from];
+                if (npcol) npcol[to] = pcol[from];
             }
         }
     }
@@ -170,23 +173,28 @@ __global__ void k_list(const uint8_t *flag, const uint64_t *pos, int64_t n, uint
         if (flag[i]) list[pos[i]] = (uint32_t)i;
 }
 
-__device__ __forceinline__ int64_t lower_key(const uint64_t *ukey, int64_t nu, uint64_t key)
+// Range [qs, qe) of the distinct batch entries of each changed row (the
+// entries are sorted by source, and every changed row has at least one).
+__global__ void k_row_ranges(const uint64_t *ukey, const uint64_t *nu_dev, const uint8_t *touched,
+                             const uint64_t *tpos, uint32_t *qs, uint32_t *qe)
 {
-    int64_t lo = 0, hi = nu;
-    while (lo < hi) {
-        const int64_t mid = (lo + hi) >> 1;
-        if (ukey[mid] < key) lo = mid + 1;
-        else hi = mid;
+    const int64_t nu = (int64_t)*nu_dev;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nu;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t j = (uint32_t)(ukey[e] >> 32);
+        if (!touched[j]) continue;
+        if (e == 0 || (uint32_t)(ukey[e - 1] >> 32) != j) qs[tpos[j]] = (uint32_t)e;
+        if (e == nu - 1 || (uint32_t)(ukey[e + 1] >> 32) != j) qe[tpos[j]] = (uint32_t)(e + 1);
     }
-    return lo;
 }
 
 // Changed rows are cut into chunks of CH old links (a row without old links
 // is one chunk), so that a long row is merged and injected by many threads.
 constexpr Off CH = 256;
 
-__global__ void k_chunk_counts(const uint32_t *tlist, int64_t nt, const Off *rp, uint32_t *cnt)
+__global__ void k_chunk_counts(const uint32_t *tlist, const uint64_t *nt_dev, const Off *rp, uint32_t *cnt)
 {
+    const int64_t nt = (int64_t)*nt_dev;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nt;
          k += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t j = tlist[k];
@@ -195,9 +203,10 @@ __global__ void k_chunk_counts(const uint32_t *tlist, int64_t nt, const Off *rp,
     }
 }
 
-__global__ void k_chunk_fill(const uint32_t *cnt, const uint64_t *cpos, int64_t nt, uint32_t *ch_row,
+__global__ void k_chunk_fill(const uint32_t *cnt, const uint64_t *cpos, const uint64_t *nt_dev, uint32_t *ch_row,
                              uint32_t *ch_idx)
 {
+    const int64_t nt = (int64_t)*nt_dev;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nt;
          k += (int64_t)gridDim.x * blockDim.x) {
         const uint64_t base = cpos[k];
@@ -226,18 +235,22 @@ __device__ __forceinline__ int64_t lower_target(const uint64_t *ukey, int64_t q,
 // element is its old position minus the deletions and plus the insertions
 // listed before it (ins_pre / del_pre: exclusive prefix counts over the
 // sorted batch).
-__global__ void k_merge_chunks(const uint32_t *ch_row, const uint32_t *ch_idx, int64_t nch, const uint32_t *tlist,
-                               const Off *rp, const int32_t *col, const double *w, const Off *nrp,
-                               const uint64_t *ukey, const uint8_t *eff, const double *uw, int64_t nu,
-                               const uint64_t *ins_pre, const uint64_t *del_pre, int32_t *ncol, double *nw)
+__global__ void k_merge_chunks(const uint32_t *ch_row, const uint32_t *ch_idx, const uint64_t *nch_dev,
+                               const uint32_t *tlist, const uint32_t *qs, const uint32_t *qes, const Off *rp,
+                               const int32_t *col, const double *w, const int32_t *pcol, const int *slot_of,
+                               const Off *nrp, const uint64_t *ukey, const uint8_t *eff, const double *uw,
+                               const uint64_t *ins_pre, const uint64_t *del_pre, int32_t *ncol, double *nw,
+                               int32_t *npcol)
 {
+    const int64_t nch = (int64_t)*nch_dev;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nch;
          t += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t j = tlist[ch_row[t]];
+        const uint32_t r = ch_row[t];
+        const uint32_t j = tlist[r];
         const Off c = ch_idx[t];
         const Off a = rp[j], b = rp[j + 1];
-        const int64_t q = lower_key(ukey, nu, (uint64_t)j << 32);
-        const int64_t qe = lower_key(ukey, nu, (uint64_t)(j + 1) << 32);
+        const int64_t q = qs[r];
+        const int64_t qe = qes[r];
         const Off i0 = a + c * CH;
         const Off i1 = (b - i0 > CH) ? i0 + CH : b;
         const uint64_t rowkey = (uint64_t)j << 32;
@@ -249,17 +262,19 @@ __global__ void k_merge_chunks(const uint32_t *ch_row, const uint32_t *ch_idx, i
         while (i < i1 || k < q1) {
             const int64_t to = i < i1 ? (int64_t)col[i] : INT64_MAX;
             const int64_t tb = k < q1 ? (int64_t)(uint32_t)ukey[k] : INT64_MAX;
-            int32_t cc = -1;
+            int32_t cc = -1, pc = 0;
             double x = 1.0;
             if (to < tb) {
                 cc = (int32_t)to;
                 x = w ? w[i] : 1.0;
+                if (npcol) pc = pcol[i];
                 i++;
             } else if (to == tb) {
                 const unsigned char e = eff[k];
                 if (e != EFF_DEL) {
                     cc = (int32_t)to;
                     x = e == EFF_UPD ? uw[k] : (w ? w[i] : 1.0);
+                    if (npcol) pc = pcol[i];
                 }
                 i++;
                 k++;
@@ -267,12 +282,17 @@ __global__ void k_merge_chunks(const uint32_t *ch_row, const uint32_t *ch_idx, i
                 if (eff[k] == EFF_INS) {
                     cc = (int32_t)tb;
                     x = uw[k];
+                    if (npcol) {
+                        const int sl = slot_of[cc];
+                        pc = sl >= 0 ? (int32_t)(0x80000000u | (unsigned)sl) : cc;
+                    }
                 }
                 k++;
             }
             if (cc >= 0) {
                 ncol[out] = cc;
                 if (nw) nw[out] = x;
+                if (npcol) npcol[out] = pc;
                 out++;
             }
         }
@@ -281,9 +301,10 @@ __global__ void k_merge_chunks(const uint32_t *ch_row, const uint32_t *ch_idx, i
 
 // Per changed row: W_j of the new row (left to right, as at creation) and the
 // change in the number of dangling nodes.
-__global__ void k_row_finish(const uint32_t *tlist, int64_t nt, const Off *rp, const Off *nrp, const double *nw,
-                             double *nwsum, long long *ddang)
+__global__ void k_row_finish(const uint32_t *tlist, const uint64_t *nt_dev, const Off *rp, const Off *nrp,
+                             const double *nw, double *nwsum, long long *ddang)
 {
+    const int64_t nt = (int64_t)*nt_dev;
     long long dd = 0;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nt;
          k += (int64_t)gridDim.x * blockDim.x) {
@@ -299,8 +320,9 @@ __global__ void k_row_finish(const uint32_t *tlist, int64_t nt, const Off *rp, c
     if (dd) atomicAdd((unsigned long long *)ddang, (unsigned long long)dd);
 }
 
-__global__ void k_flags(const uint8_t *eff, int64_t nu, uint8_t *ins, uint8_t *del)
+__global__ void k_flags(const uint8_t *eff, const uint64_t *nu_dev, uint8_t *ins, uint8_t *del)
 {
+    const int64_t nu = (int64_t)*nu_dev;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nu;
          k += (int64_t)gridDim.x * blockDim.x) {
         ins[k] = eff[k] == EFF_INS;
@@ -310,10 +332,11 @@ __global__ void k_flags(const uint8_t *eff, int64_t nu, uint8_t *ins, uint8_t *d
 
 // F += sign * d H_j P[:, j] for the listed columns, one warp per chunk of CH
 // links of a column.
-__global__ void k_inject_chunks(const uint32_t *ch_row, const uint32_t *ch_idx, int64_t nch, const uint32_t *tlist,
-                                const Off *rp, const int32_t *col, const double *w, const double *wsum,
-                                const double *H, double sd, double *F)
+__global__ void k_inject_chunks(const uint32_t *ch_row, const uint32_t *ch_idx, const uint64_t *nch_dev,
+                                const uint32_t *tlist, const Off *rp, const int32_t *col, const double *w,
+                                const double *wsum, const double *H, double sd, double *F)
 {
+    const int64_t nch = (int64_t)*nch_dev;
     const int lane = threadIdx.x & 31;
     const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < nch; t += nwarp) {
@@ -322,8 +345,14 @@ __global__ void k_inject_chunks(const uint32_t *ch_row, const uint32_t *ch_idx, 
         const Off i0 = a + ch_idx[t] * CH;
         if (i0 >= b) continue;
         const Off i1 = (b - i0 > CH) ? i0 + CH : b;
-        const double h = sd * H[j];
-        const double unit = w ? h / wsum[j] : h / (double)(b - a);
+        // one FP64 division per chunk (lane 0), not one per lane: FP64 issue
+        // is scarce on this part
+        double unit = 0.0;
+        if (lane == 0) {
+            const double h = sd * H[j];
+            unit = w ? h / wsum[j] : h / (double)(b - a);
+        }
+        unit = __shfl_sync(FULL, unit, 0);
         for (Off e = i0 + lane; e < i1; e += 32) atomicAdd(F + col[e], w ? unit * w[e] : unit);
     }
 }
@@ -371,22 +400,30 @@ di_status update_edges(di_graph_s *g, di_state_s *st, int64_t m, const int32_t *
     for (int x = 0; x < bb; x += 8) { lo[np] = x; cnt[np] = bb - x < 8 ? bb - x : 8; np++; }
     for (int x = 0; x < bb; x += 8) { lo[np] = 32 + x; cnt[np] = bb - x < 8 ? bb - x : 8; np++; }
     DI_TRY(radix_sort_pairs(&keys, &vals, &keys2, &vals2, m, lo, cnt, np, s));
-    // 2. one entry per distinct link: the last operation on it
+    // 2. one entry per distinct link: the last operation on it.  Counts that
+    // only the device knows (distinct links nu, changed rows nt, chunks) stay
+    // on the device: the arrays are sized by their bounds and the kernels
+    // that depend on a count read it there, so the whole update runs without
+    // a host round trip until the new link count is read at the end.
+    const unsigned pgrid = (unsigned)(8 * sm_count(g->device));   // grid of the count-driven kernels
+    uint64_t *nu_dev, *mnew_dev, *nt_dev, *och_dev, *nch_dev;
+    DI_TRY(t.get(&nu_dev, 1));
+    DI_TRY(t.get(&mnew_dev, 1));
+    DI_TRY(t.get(&nt_dev, 1));
+    DI_TRY(t.get(&och_dev, 1));
+    DI_TRY(t.get(&nch_dev, 1));
     k_run_ends<<<grid_for(m, 256), 256, 0, s>>>(keys, m, keep);
     count_launches(1);
-    DI_TRY(scan_exclusive<uint8_t>(keep, pos, m, total, s));
-    uint64_t nu = 0;
-    DI_CUDA(cudaMemcpyAsync(&nu, total, sizeof(nu), cudaMemcpyDeviceToHost, s));
-    DI_CUDA(cudaStreamSynchronize(s));
+    DI_TRY(scan_exclusive<uint8_t>(keep, pos, m, nu_dev, s));
     uint64_t *ukey;
     int8_t *uop;
     double *uw;
     uint8_t *eff, *touched;
     int *delta;
-    DI_TRY(t.get(&ukey, nu));
-    DI_TRY(t.get(&uop, nu));
-    DI_TRY(t.get(&uw, nu));
-    DI_TRY(t.get(&eff, nu));
+    DI_TRY(t.get(&ukey, m));
+    DI_TRY(t.get(&uop, m));
+    DI_TRY(t.get(&uw, m));
+    DI_TRY(t.get(&eff, m));
     DI_TRY(t.get(&touched, n));
     DI_TRY(t.get(&delta, n));
     DI_CUDA(cudaMemsetAsync(touched, 0, n, s));
@@ -396,107 +433,107 @@ di_status update_edges(di_graph_s *g, di_state_s *st, int64_t m, const int32_t *
     count_launches(1);
     // 3. classify against the old rows
     const Off *rp = static_cast<const Off *>(g->rp);
-    k_classify<<<grid_for((int64_t)nu, 256), 256, 0, s>>>(ukey, uop, uw, (int64_t)nu, rp, g->col, g->w, eff, delta,
-                                                          touched, g->indeg);
+    k_classify<<<pgrid, 256, 0, s>>>(ukey, uop, uw, nu_dev, rp, g->col, g->w, eff, delta, touched, g->indeg);
     count_launches(1);
-    // 4. new row pointers
+    // 4. new row pointers (at most m links more than before)
     uint32_t *deg;
     uint64_t *ex;
     DI_TRY(t.get(&deg, n));
     DI_TRY(t.get(&ex, n));
     k_new_degree<<<grid_for(n, 256), 256, 0, s>>>(rp, delta, n, deg);
     count_launches(1);
-    DI_TRY(scan_exclusive<uint32_t>(deg, ex, n, total, s));
-    uint64_t mnew = 0;
-    DI_CUDA(cudaMemcpyAsync(&mnew, total, sizeof(mnew), cudaMemcpyDeviceToHost, s));
-    DI_CUDA(cudaStreamSynchronize(s));
-    int32_t *ncol = nullptr;
+    DI_TRY(scan_exclusive<uint32_t>(deg, ex, n, mnew_dev, s));
+    const int64_t cap = nnz + m;
+    // the tagged push copy of the links is carried over (same hot pages) for
+    // unweighted graphs; a weighted graph rebuilds it with its FP32 weights
+    const bool carry_pcol = !g->weighted && g->pcol && g->slot_of && g->pcol_version == g->version;
+    int32_t *ncol = nullptr, *npcol = nullptr;
     double *nwv = nullptr, *nwsum = nullptr;
     Off *nrp = nullptr;
-    DI_TRY(dalloc_t(&ncol, mnew, s));
+    DI_TRY(dalloc_t(&ncol, cap, s));
+    if (carry_pcol) DI_TRY(dalloc_t(&npcol, cap, s));
     DI_TRY(dalloc_t(&nrp, n + 1 + RP_PAD, s));
     DI_CUDA(cudaMemsetAsync(nrp + n + 1, 0, sizeof(Off) * RP_PAD, s));
     if (g->weighted) {
-        DI_TRY(dalloc_t(&nwv, mnew, s));
+        DI_TRY(dalloc_t(&nwv, cap, s));
         DI_TRY(dalloc_t(&nwsum, n, s));
         DI_CUDA(cudaMemcpyAsync(nwsum, g->wsum, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
     }
-    k_rp_from_scan<<<grid_for(n + 1, 256), 256, 0, s>>>(ex, total, n, nrp);
+    k_rp_from_scan<<<grid_for(n + 1, 256), 256, 0, s>>>(ex, mnew_dev, n, nrp);
     count_launches(1);
     // 5. unchanged rows move, changed rows are merged
-    k_copy_rows<<<grid_for(n, 256), 256, 0, s>>>(rp, nrp, g->col, g->w, touched, n, ncol, nwv);
+    k_copy_rows<<<grid_for(n, 256), 256, 0, s>>>(rp, nrp, g->col, g->w, g->pcol, touched, n, ncol, nwv, npcol);
     count_launches(1);
+    const int64_t tcap = (n < m ? n : m) + 1;   // changed rows: at most one per distinct batch link
     uint64_t *tpos;
     DI_TRY(t.get(&tpos, n));
-    DI_TRY(scan_exclusive<uint8_t>(touched, tpos, n, total, s));
-    uint64_t nt = 0;
-    DI_CUDA(cudaMemcpyAsync(&nt, total, sizeof(nt), cudaMemcpyDeviceToHost, s));
-    DI_CUDA(cudaStreamSynchronize(s));
-    uint32_t *tlist;
+    DI_TRY(scan_exclusive<uint8_t>(touched, tpos, n, nt_dev, s));
+    uint32_t *tlist, *qs, *qe;
     long long *ddang;
-    DI_TRY(t.get(&tlist, nt));
+    DI_TRY(t.get(&tlist, tcap));
+    DI_TRY(t.get(&qs, tcap));
+    DI_TRY(t.get(&qe, tcap));
     DI_TRY(t.get(&ddang, 1));
     DI_CUDA(cudaMemsetAsync(ddang, 0, sizeof(long long), s));
     k_list<<<grid_for(n, 256), 256, 0, s>>>(touched, tpos, n, tlist);
-    count_launches(1);
-    // insertions / deletions before each batch entry (exclusive counts)
+    k_row_ranges<<<pgrid, 256, 0, s>>>(ukey, nu_dev, touched, tpos, qs, qe);
+    count_launches(2);
+    // insertions / deletions before each batch entry (exclusive counts; the
+    // flags past the last distinct entry stay 0)
     uint8_t *fins, *fdel;
     uint64_t *ins_pre, *del_pre;
-    DI_TRY(t.get(&fins, nu + 1));
-    DI_TRY(t.get(&fdel, nu + 1));
-    DI_TRY(t.get(&ins_pre, nu + 1));
-    DI_TRY(t.get(&del_pre, nu + 1));
-    DI_CUDA(cudaMemsetAsync(fins + nu, 0, 1, s));
-    DI_CUDA(cudaMemsetAsync(fdel + nu, 0, 1, s));
-    k_flags<<<grid_for((int64_t)nu, 256), 256, 0, s>>>(eff, (int64_t)nu, fins, fdel);
+    DI_TRY(t.get(&fins, m + 1));
+    DI_TRY(t.get(&fdel, m + 1));
+    DI_TRY(t.get(&ins_pre, m + 1));
+    DI_TRY(t.get(&del_pre, m + 1));
+    DI_CUDA(cudaMemsetAsync(fins, 0, m + 1, s));
+    DI_CUDA(cudaMemsetAsync(fdel, 0, m + 1, s));
+    k_flags<<<pgrid, 256, 0, s>>>(eff, nu_dev, fins, fdel);
     count_launches(1);
-    DI_TRY(scan_exclusive<uint8_t>(fins, ins_pre, (int64_t)nu + 1, nullptr, s));
-    DI_TRY(scan_exclusive<uint8_t>(fdel, del_pre, (int64_t)nu + 1, nullptr, s));
-    // chunks of the changed rows, old and new
+    DI_TRY(scan_exclusive<uint8_t>(fins, ins_pre, m + 1, nullptr, s));
+    DI_TRY(scan_exclusive<uint8_t>(fdel, del_pre, m + 1, nullptr, s));
+    // chunks of the changed rows, old and new (counts past nt stay 0)
     uint32_t *ocnt, *ncnt;
-    uint64_t *ocpos, *ncpos, *ototal, *ntotal;
-    DI_TRY(t.get(&ocnt, nt + 1));
-    DI_TRY(t.get(&ncnt, nt + 1));
-    DI_TRY(t.get(&ocpos, nt + 1));
-    DI_TRY(t.get(&ncpos, nt + 1));
-    DI_TRY(t.get(&ototal, 1));
-    DI_TRY(t.get(&ntotal, 1));
-    k_chunk_counts<<<grid_for((int64_t)nt, 256), 256, 0, s>>>(tlist, (int64_t)nt, rp, ocnt);
-    k_chunk_counts<<<grid_for((int64_t)nt, 256), 256, 0, s>>>(tlist, (int64_t)nt, nrp, ncnt);
+    uint64_t *ocpos, *ncpos;
+    DI_TRY(t.get(&ocnt, tcap));
+    DI_TRY(t.get(&ncnt, tcap));
+    DI_TRY(t.get(&ocpos, tcap));
+    DI_TRY(t.get(&ncpos, tcap));
+    DI_CUDA(cudaMemsetAsync(ocnt, 0, sizeof(uint32_t) * tcap, s));
+    DI_CUDA(cudaMemsetAsync(ncnt, 0, sizeof(uint32_t) * tcap, s));
+    k_chunk_counts<<<pgrid, 256, 0, s>>>(tlist, nt_dev, rp, ocnt);
+    k_chunk_counts<<<pgrid, 256, 0, s>>>(tlist, nt_dev, nrp, ncnt);
     count_launches(2);
-    DI_TRY(scan_exclusive<uint32_t>(ocnt, ocpos, (int64_t)nt, ototal, s));
-    DI_TRY(scan_exclusive<uint32_t>(ncnt, ncpos, (int64_t)nt, ntotal, s));
-    uint64_t hch[2] = {0, 0};
-    DI_CUDA(cudaMemcpyAsync(hch, ototal, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
-    DI_CUDA(cudaMemcpyAsync(hch + 1, ntotal, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
-    DI_CUDA(cudaStreamSynchronize(s));
+    DI_TRY(scan_exclusive<uint32_t>(ocnt, ocpos, tcap, och_dev, s));
+    DI_TRY(scan_exclusive<uint32_t>(ncnt, ncpos, tcap, nch_dev, s));
+    // a row of d links has ceil(d / CH) chunks (1 if empty)
+    const int64_t ocap = nnz / CH + tcap + 1, ncap = cap / CH + tcap + 1;
     uint32_t *och_row, *och_idx, *nch_row, *nch_idx;
-    DI_TRY(t.get(&och_row, hch[0] + 1));
-    DI_TRY(t.get(&och_idx, hch[0] + 1));
-    DI_TRY(t.get(&nch_row, hch[1] + 1));
-    DI_TRY(t.get(&nch_idx, hch[1] + 1));
-    k_chunk_fill<<<grid_for((int64_t)nt, 256), 256, 0, s>>>(ocnt, ocpos, (int64_t)nt, och_row, och_idx);
-    k_chunk_fill<<<grid_for((int64_t)nt, 256), 256, 0, s>>>(ncnt, ncpos, (int64_t)nt, nch_row, nch_idx);
+    DI_TRY(t.get(&och_row, ocap));
+    DI_TRY(t.get(&och_idx, ocap));
+    DI_TRY(t.get(&nch_row, ncap));
+    DI_TRY(t.get(&nch_idx, ncap));
+    k_chunk_fill<<<pgrid, 256, 0, s>>>(ocnt, ocpos, nt_dev, och_row, och_idx);
+    k_chunk_fill<<<pgrid, 256, 0, s>>>(ncnt, ncpos, nt_dev, nch_row, nch_idx);
     count_launches(2);
-    k_merge_chunks<<<grid_for((int64_t)hch[0], 128), 128, 0, s>>>(och_row, och_idx, (int64_t)hch[0], tlist, rp, g->col,
-                                                                   g->w, nrp, ukey, eff, uw, (int64_t)nu, ins_pre,
-                                                                   del_pre, ncol, nwv);
+    k_merge_chunks<<<pgrid, 128, 0, s>>>(och_row, och_idx, och_dev, tlist, qs, qe, rp, g->col, g->w, g->pcol,
+                                         g->slot_of, nrp, ukey, eff, uw, ins_pre, del_pre, ncol, nwv, npcol);
     count_launches(1);
-    k_row_finish<<<grid_for((int64_t)nt, 128), 128, 0, s>>>(tlist, (int64_t)nt, rp, nrp, nwv, nwsum, ddang);
+    k_row_finish<<<pgrid, 128, 0, s>>>(tlist, nt_dev, rp, nrp, nwv, nwsum, ddang);
     count_launches(1);
     // 6. F += d (P' - P) H: withdraw the old columns, inject the new ones
-    if (st && nt) {
-        k_inject_chunks<<<grid_for((int64_t)hch[0] * 32, 256), 256, 0, s>>>(och_row, och_idx, (int64_t)hch[0], tlist,
-                                                                          rp, g->col, g->w, g->wsum, st->H,
-                                                                          -st->d, st->F);
-        k_inject_chunks<<<grid_for((int64_t)hch[1] * 32, 256), 256, 0, s>>>(nch_row, nch_idx, (int64_t)hch[1], tlist,
-                                                                          nrp, ncol, nwv, nwsum, st->H, st->d,
-                                                                          st->F);
+    if (st) {
+        k_inject_chunks<<<pgrid, 256, 0, s>>>(och_row, och_idx, och_dev, tlist, rp, g->col, g->w, g->wsum, st->H,
+                                             -st->d, st->F);
+        k_inject_chunks<<<pgrid, 256, 0, s>>>(nch_row, nch_idx, nch_dev, tlist, nrp, ncol, nwv, nwsum, st->H, st->d,
+                                             st->F);
         count_launches(2);
     }
     DI_CUDA(cudaGetLastError());
     long long hd = 0;
+    uint64_t mnew = 0;
     DI_CUDA(cudaMemcpyAsync(&hd, ddang, sizeof(hd), cudaMemcpyDeviceToHost, s));
+    DI_CUDA(cudaMemcpyAsync(&mnew, mnew_dev, sizeof(mnew), cudaMemcpyDeviceToHost, s));
     DI_CUDA(cudaStreamSynchronize(s));
 
     // install P'
@@ -511,6 +548,12 @@ di_status update_edges(di_graph_s *g, di_state_s *st, int64_t m, const int32_t *
     g->col = ncol;
     g->w = nwv;
     g->wsum = nwsum;
+    if (carry_pcol) {
+        // the caller bumps the version after a successful update
+        dfree(g->pcol, s);
+        g->pcol = npcol;
+        g->pcol_version = g->version + 1;
+    }
     g->cp = nullptr;
     g->crow = nullptr;
     g->cw = nullptr;
