@@ -49,7 +49,8 @@ typedef enum {
     DI_ERR_OOM = 3,            /* device or host allocation failed                 */
     DI_ERR_NOT_CONVERGED = 4,  /* sweep cap reached; outputs hold the best state   */
     DI_ERR_CUDA = 5,           /* a CUDA runtime call failed                       */
-    DI_ERR_DEVICE_TIMEOUT = 6  /* a bounded device-side wait gave up               */
+    DI_ERR_DEVICE_TIMEOUT = 6  /* reserved: no kernel of this library waits on
+                                  another, so no call returns it                  */
 } di_status;
 
 enum { DI_LAYOUT_CSR = 0, DI_LAYOUT_CSC = 1 };
@@ -320,10 +321,13 @@ di_status di_residual_l1(di_graph_t g, const double *v, double *out, int mem, vo
  * the device: a serving loop whose device memory is entirely reserved by its
  * own pool, or a caller that cannot afford the implicit device-wide
  * synchronisation that cudaMalloc / cudaFree may cause.
- *   v       float64[n] in DEVICE memory (host vectors are refused: staging
- *           them would need an allocation)
+ *   v       float64[n] in DEVICE (or managed) memory of the graph's device;
+ *           anything else, host memory included, returns DI_ERR_INVALID_ARG
+ *           before any work is queued (staging a host vector would need an
+ *           allocation)
  *   out     host double receiving |v|_1
- * Scratch: one static device array of about 1 MiB in libdi.so, present on
+ * Scratch: one static device array of about 256 KiB (256 bytes of control
+ * block and two float64 partials per 8,192-node tile) in libdi.so, present on
  * every device that loads the library until the process exits; it limits the
  * graph to n <= 2^16 * 2048 = 134,217,728 nodes (larger graphs return
  * DI_ERR_INVALID_ARG).  The first call made on a device looks up the array's

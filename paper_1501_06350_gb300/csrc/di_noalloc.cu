@@ -47,6 +47,16 @@ extern "C" di_status di_residual_l1_noalloc(di_graph_t g, const double *v, doubl
 {
     if (!g || !v || !out) return DI_ERR_INVALID_ARG;
     if (g->n > NOALLOC_MAX_NODES) return DI_ERR_INVALID_ARG;
+    // v must be device (or managed) memory of the graph's device: a host
+    // vector would have to be staged through an allocation, and a kernel must
+    // never be handed a host address
+    cudaPointerAttributes pa;
+    if (cudaPointerGetAttributes(&pa, v) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return DI_ERR_INVALID_ARG;
+    }
+    if ((pa.type != cudaMemoryTypeDevice && pa.type != cudaMemoryTypeManaged) || pa.device != g->device)
+        return DI_ERR_INVALID_ARG;
     int prev = -1;
     if (cudaGetDevice(&prev) != cudaSuccess) return DI_ERR_CUDA;
     if (prev != g->device && cudaSetDevice(g->device) != cudaSuccess) return DI_ERR_CUDA;

@@ -53,8 +53,26 @@ def test_noalloc_matches_allocating_entry_point(lib, n):
             L.check(L.lib().di_residual_l1_noalloc(h, ptr, ctypes.byref(got), stream),
                     "di_residual_l1_noalloc")
             exact = math.fsum(np.abs(v.cpu().numpy()))
-            assert abs(got.value - ref.value) <= n * 2.3e-16 * exact
+            # same kernel, same fixed summation order: the same double
+            assert got.value == ref.value
             assert abs(got.value - exact) <= n * 2.3e-16 * exact
+    finally:
+        L.lib().di_graph_destroy(h)
+
+
+def test_noalloc_refuses_host_vectors(lib):
+    # a host vector is refused on the host (DI_ERR_INVALID_ARG); nothing is launched
+    L = lib
+    n = 3000
+    h = _graph(L, n)
+    try:
+        v = np.random.default_rng(3).standard_normal(n)
+        out = ctypes.c_double(-1.0)
+        rc = L.lib().di_residual_l1_noalloc(h, v.ctypes.data_as(ctypes.c_void_p), ctypes.byref(out), None)
+        assert rc == L.DI_ERR_INVALID_ARG and out.value == -1.0
+        pinned = torch.from_numpy(v).pin_memory()
+        rc = L.lib().di_residual_l1_noalloc(h, ctypes.c_void_p(pinned.data_ptr()), ctypes.byref(out), None)
+        assert rc == L.DI_ERR_INVALID_ARG and out.value == -1.0
     finally:
         L.lib().di_graph_destroy(h)
 
