@@ -226,7 +226,9 @@ def test_adjoint_full_size(di):
     lambda against the oracle's Jacobi solution in the infinity norm."""
     g = web2m_w()
     G = di.Graph(g.n, g.ptr, g.idx, g.w)
-    cp, ci, cw = G.export_csr()
+    cp, ci, cw = oracle.canonical_csr(g.n, g.ptr, g.idx, g.w)
+    gp_, gi_, gw_ = G.export_csr()
+    assert np.array_equal(_np(gp_), cp) and np.array_equal(_np(gi_), ci) and np.array_equal(_np(gw_), cw)
     gv = np.random.default_rng(11).standard_normal(g.n)
     x, _, _ = di.solve(G, D, tol=1e-10)
     lam, gz, gw, info = di.adjoint(G, D, gv, x, tol=1e-10)

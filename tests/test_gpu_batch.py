@@ -172,7 +172,9 @@ def test_batch_full_size(di):
     G = di.Graph(g.n, g.ptr, g.idx)
     H, res, info = di.solve_batch(G, Z, D, tol=1e-9)
     assert info["converged"]
-    cp, ci, _ = G.export_csr()
+    cp, ci, _ = oracle.canonical_csr(g.n, g.ptr, g.idx)
+    gp_, gi_, _ = G.export_csr()
+    assert np.array_equal(_np(gp_), cp) and np.array_equal(_np(gi_), ci)
     H = _np(H)
     for c in (0, 31, 63):
         x, _, _, _ = oracle.di_solve(g.n, cp, ci, None, D, Z[:, c], tol=1e-12)
