@@ -140,7 +140,6 @@ struct DevCtl {
     unsigned long long edge_pushes;
     unsigned long long sweep;         // pushes performed by this call
     unsigned long long max_sweeps;
-    unsigned long long nhub;          // selected hub nodes appended by the running selection
     unsigned long long npieces;       // hub pieces cut by the plan (read by the push)
     unsigned long long sweep_links;   // links pushed by the running push
     unsigned long long nent;          // frontier nodes of the last selection (mask bits)
@@ -162,6 +161,7 @@ struct GraphPtrs {
     const double *w;
     const float *w32;
     unsigned *hub_list;
+    uint64_t hub_cap;         // entries of hub_list
     uint32_t *pc_row;
     uint32_t *pc_len;
     double *pc_val;
@@ -204,6 +204,8 @@ struct di_state_s {
     double *pc_val = nullptr;
     // per-tile partials
     unsigned int *tile_cnt = nullptr;
+    unsigned int *tile_hub = nullptr;        // selected hubs of each tile (listed from hub_base[tile] on)
+    uint64_t *hub_base = nullptr;            // first hub-list slot of each tile (its hub nodes before it)
     unsigned int *tile_diff = nullptr;
     float *tile_l1f = nullptr;               // |F|_1 partial, FP32 rounded upward
     unsigned *tile_maxf = nullptr;           // max |F_i|, FP32 bits rounded downward

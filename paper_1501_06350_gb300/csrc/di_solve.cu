@@ -376,7 +376,6 @@ __global__ void __launch_bounds__(SEL_THREADS) k_reduce(const double *v, const d
         if (mode == RED_INIT || mode == RED_CYCLE) {
             // a loop that ended in its stop test leaves the hubs of its last
             // selection listed (nobody took them): start the next one clean
-            ctl->nhub = 0;
             ctl->npieces = 0;
             ctl->push_ready = 0;
             ctl->l1 = sa;
@@ -475,23 +474,74 @@ __device__ __forceinline__ unsigned theta_word(double th, const float *)
 }
 
 // --------------------------------------------------------------- select
+// One CTA of SEL_THREADS per tile of TILE nodes.  The tile is read in
+// SEL_ROUNDS rounds; in round q warp w covers the 64 nodes
+// tile + q * 2 SEL_THREADS + 64 w, lane l its nodes l and 32 + l, so every
+// load instruction of a warp reads 32 consecutive words (coalesced) and every
+// frontier mask word is one warp ballot.  Per node: the exact DI-argmax test
+// on the raw fluid word, and FP32 upper-bound partials of |F|_1 and of
+// max |F_i| taken from the word's upper 32 bits (sign, exponent, 20 mantissa
+// bits), which bound |x| from below as they are and from above with one
+// unit added in their last place (at most 2^-20 above |x|).  Selected hubs
+// are listed in the tile's own region of the hub list (no global atomics).
+// Fluid arrays hold whole tiles, zero past n, so the tail needs no test.
+__device__ __forceinline__ unsigned hi_word(unsigned long long b) { return (unsigned)(b >> 32); }
+__device__ __forceinline__ unsigned hi_word(unsigned b) { return b; }
+// FP32 bits bounding |x| from above, from the upper word of its FP64 bits
+// (0 stays 0: a zero word never contributes).
+__device__ __forceinline__ unsigned up_hi(unsigned hi, bool nonzero)
+{
+    if (hi < 0x38100000u) return nonzero ? 0x00800000u : 0u;   // below FLT_MIN: FLT_MIN
+    if (hi >= 0x47f00000u) return 0x7f800000u;                 // beyond FLT_MAX: +inf
+    return ((hi - 0x38000000u) << 3) + 8u;
+}
+// FP32 bits bounding |x| from below (truncation to the FP32 grid).
+__device__ __forceinline__ unsigned down_hi(unsigned hi)
+{
+    if (hi < 0x38100000u) return 0u;
+    if (hi >= 0x47f00000u) return 0x7f7fffffu;
+    return (hi - 0x38000000u) << 3;
+}
+
+constexpr int SEL_ROUNDS = TILE / (2 * SEL_THREADS);   // rounds of 64 nodes per warp
+constexpr int SEL_WORDS = TILE / 32;                   // mask words per tile
+
 template <typename T>
 __global__ void __launch_bounds__(SEL_THREADS)
     k_select(const T *F, int64_t n, unsigned *mask, const unsigned *__restrict__ hubbits,
-             const GraphPtrs *__restrict__ gp, unsigned *tile_cnt, unsigned *tile_diff, float *tile_l1f,
-             unsigned *tile_maxf, unsigned *tile_maxu, DevCtl *ctl, int use_cond, cudaGraphConditionalHandle cond,
-             int32_t *sel_ids)
+             const GraphPtrs *__restrict__ gp, const uint64_t *__restrict__ hub_base, unsigned *tile_hub,
+             unsigned *tile_cnt, unsigned *tile_diff, float *tile_l1f, unsigned *tile_maxf, unsigned *tile_maxu,
+             DevCtl *ctl, int use_cond, cudaGraphConditionalHandle cond, int32_t *sel_ids)
 {
     typedef typename FluidWord<T>::U U;
-    constexpr int P = SEL_PER_THREAD;
+    constexpr bool F64 = sizeof(U) == 8;
+    constexpr int R = SEL_ROUNDS;
     constexpr int NW = SEL_THREADS / 32;
-    static_assert(32 % P == 0, "a mask word must cover whole threads");
     static_assert(TILE <= 65535, "per-tile counts are packed in 16 bits");
+    static_assert(R * 2 * SEL_THREADS == TILE, "whole rounds per tile");
     __shared__ float s_fx[NW];
-    __shared__ unsigned s_mx[NW], s_mu[NW], s_cnt[NW];
-    __shared__ unsigned long long smu[NW + 1];
+    __shared__ unsigned s_mx[NW], s_mu[NW], s_cnt[NW], s_hub[NW];
+    __shared__ unsigned s_hubw[NW][2 * R];     // each warp's selected-hub words
+    __shared__ unsigned s_selw[SEL_WORDS];     // selected words in node order (verification output)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t tile = blockIdx.x;
+    const int64_t t0 = tile * TILE;
+    const unsigned long long keep = pol_last();
+    // the fluid words are requested before the control block is read, so the
+    // two round trips overlap (F is readable whatever the block says)
+    U fb[2 * R];
+#pragma unroll
+    for (int q = 0; q < R; q++) {
+        const int64_t seg = t0 + (int64_t)q * 2 * SEL_THREADS + 64 * warp;
+        fb[2 * q] = ld_word(F + seg + lane, keep);
+        fb[2 * q + 1] = ld_word(F + seg + 32 + lane, keep);
+    }
+    // control fields: independent L2 loads (not volatile ones, which would
+    // be issued one after another)
+    const unsigned done0 = __ldcg(&ctl->done);
+    const double theta0 = __ldcg(&ctl->theta);
     volatile DevCtl *vc = ctl;
-    if (vc->done) {
+    if (done0) {
         // Nothing left to do: the push that follows must find no work, and a
         // graph while-loop must end here too.
         if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -501,68 +551,35 @@ __global__ void __launch_bounds__(SEL_THREADS)
         return;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) vc->npieces = 0;   // the last push is over
-    const U tb = theta_word(vc->theta, F);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t tile = blockIdx.x;
-    const int64_t i0 = tile * TILE + (int64_t)threadIdx.x * P;
-    const unsigned long long keep = pol_last();
-
-    U fb[P];
-    loadw_keep<P>(F, i0, n, fb, keep);
-    const unsigned hubw = (__ldg(hubbits + i0 / 32) >> (i0 % 32)) & ((1u << P) - 1u);
+    // a selected node holds fluid (the zero words past n never qualify, even
+    // at theta = 0)
+    U tb = theta_word(theta0, F);
+    tb = tb > (U)1 ? tb : (U)1;
     float fx = 0.0f;
-    unsigned selm = 0;
-    unsigned mb = 0, mu = 0;
+    unsigned hmax = 0, nbits = 0, nsel = 0, nhubs = 0;
 #pragma unroll
-    for (int k = 0; k < P; k++) {
+    for (int k = 0; k < 2 * R; k++) {
+        const int q = k >> 1, h = k & 1;
+        const int wt = 32 * q + 2 * warp + h;              // mask word inside the tile
         const U b = fb[k] & FluidWord<T>::ABS;
-        const unsigned bu = up32(b);
-        fx = __fadd_ru(fx, __uint_as_float(bu));
-        if ((i0 + k < n) && b != 0 && b >= tb) selm |= 1u << k;
-        const unsigned md = down32(b);
-        mb = md > mb ? md : mb;
-        mu = bu > mu ? bu : mu;
-    }
-    const unsigned bits = selm & ~hubw;   // taken by the push
-    const unsigned hubs = selm & hubw;    // taken by the plan
-    unsigned *hub_list = gp->hub_list;
-    // selected hubs: one list reservation per warp
-    {
-        const unsigned nh = __popc(hubs);
-        unsigned incl = nh;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const unsigned y = __shfl_up_sync(FULL, incl, o);
-            if (lane >= o) incl += y;
+        const unsigned sw = __ballot_sync(FULL, b >= tb);
+        const unsigned hw = __ldg(hubbits + tile * SEL_WORDS + wt);
+        const unsigned hi = hi_word(b);
+        fx = __fadd_ru(fx, __uint_as_float(F64 ? up_hi(hi, b != 0) : hi));
+        hmax = hi > hmax ? hi : hmax;
+        const unsigned bits = sw & ~hw;   // taken by the push
+        const unsigned hs = sw & hw;      // taken by the plan
+        if (lane == 0) {
+            mask[tile * SEL_WORDS + wt] = bits;
+            s_hubw[warp][k] = hs;
+            if (sel_ids) s_selw[wt] = sw;
         }
-        const unsigned wtot = __shfl_sync(FULL, incl, 31);
-        if (wtot) {
-            unsigned long long wbase = 0;
-            if (lane == 31) wbase = atomicAdd((unsigned long long *)&ctl->nhub, (unsigned long long)wtot);
-            wbase = __shfl_sync(FULL, wbase, 31);
-            unsigned long long pb = wbase + incl - nh;
-#pragma unroll
-            for (int k = 0; k < P; k++)
-                if ((hubs >> k) & 1u) hub_list[pb++] = (unsigned)(i0 + k);
-        }
+        nbits += __popc(bits);
+        nsel += __popc(sw);
+        nhubs += __popc(hs);
     }
-    // mask word of 32 consecutive nodes = OR over 32 / P threads
-    {
-        unsigned word = bits << (P * (lane % (32 / P)));
-#pragma unroll
-        for (int o = 1; o < 32 / P; o <<= 1) word |= __shfl_xor_sync(FULL, word, o);
-        if (lane % (32 / P) == 0) mask[i0 / 32] = word;
-    }
-    // verification output: ascending ids of the selected nodes inside the tile
-    if (sel_ids) {
-        unsigned long long tot;
-        unsigned long long spos = block_exscan_u64<SEL_THREADS>((unsigned long long)__popc(selm), smu, &tot);
-#pragma unroll
-        for (int k = 0; k < P; k++)
-            if ((selm >> k) & 1u) sel_ids[tile * TILE + (int64_t)(spos++)] = (int32_t)(i0 + k);
-    }
-    // tile partials in a fixed order (warp butterfly, then warps in order)
-    unsigned cnt = (unsigned)__popc(bits) | ((unsigned)__popc(selm) << 16);
+    // tile partials in a fixed order (warp butterfly, then warp 0 over the warps)
+    unsigned mb = F64 ? down_hi(hmax) : hmax, mu = F64 ? up_hi(hmax, hmax != 0) : hmax;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         fx = __fadd_ru(fx, __shfl_xor_sync(FULL, fx, o));
@@ -570,30 +587,86 @@ __global__ void __launch_bounds__(SEL_THREADS)
         mb = y > mb ? y : mb;
         const unsigned yu = __shfl_xor_sync(FULL, mu, o);
         mu = yu > mu ? yu : mu;
-        cnt += __shfl_xor_sync(FULL, cnt, o);
     }
     if (lane == 0) {
         s_fx[warp] = fx;
         s_mx[warp] = mb;
         s_mu[warp] = mu;
-        s_cnt[warp] = cnt;
+        s_cnt[warp] = nbits | (nsel << 16);
+        s_hub[warp] = nhubs;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        float t = s_fx[0];
-        unsigned mx = s_mx[0], mxu = s_mu[0], c = s_cnt[0];
+    // selected hubs: the warps' lists one after another in the tile's region
+    if (nhubs) {
+        uint64_t pb = hub_base[tile];
+        for (int w = 0; w < warp; w++) pb += s_hub[w];
+        unsigned *hub_list = gp->hub_list;
+        const unsigned lt = (1u << lane) - 1u;
 #pragma unroll
-        for (int w = 1; w < NW; w++) {
-            t = __fadd_ru(t, s_fx[w]);
-            mx = s_mx[w] > mx ? s_mx[w] : mx;
-            mxu = s_mu[w] > mxu ? s_mu[w] : mxu;
-            c += s_cnt[w];
+        for (int k = 0; k < 2 * R; k++) {
+            const unsigned hs = s_hubw[warp][k];
+            if ((hs >> lane) & 1u)
+                hub_list[pb + __popc(hs & lt)] =
+                    (unsigned)(t0 + (int64_t)(k >> 1) * 2 * SEL_THREADS + 64 * warp + 32 * (k & 1) + lane);
+            pb += __popc(hs);
         }
-        tile_l1f[tile] = t;
-        tile_maxf[tile] = mx;
-        tile_maxu[tile] = mxu;
-        tile_cnt[tile] = c & 0xffffu;
-        tile_diff[tile] = c >> 16;
+    }
+    if (warp == 0) {
+        float t = lane < NW ? s_fx[lane] : 0.0f;
+        unsigned mx = lane < NW ? s_mx[lane] : 0u, mxu = lane < NW ? s_mu[lane] : 0u;
+        unsigned c = lane < NW ? s_cnt[lane] : 0u, nh = lane < NW ? s_hub[lane] : 0u;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            t = __fadd_ru(t, __shfl_xor_sync(FULL, t, o));
+            const unsigned y = __shfl_xor_sync(FULL, mx, o);
+            mx = y > mx ? y : mx;
+            const unsigned yu = __shfl_xor_sync(FULL, mxu, o);
+            mxu = yu > mxu ? yu : mxu;
+            c += __shfl_xor_sync(FULL, c, o);
+            nh += __shfl_xor_sync(FULL, nh, o);
+        }
+        if (lane == 0) {
+            tile_l1f[tile] = t;
+            tile_maxf[tile] = mx;
+            tile_maxu[tile] = mxu;
+            tile_cnt[tile] = c & 0xffffu;
+            tile_diff[tile] = c >> 16;
+            tile_hub[tile] = nh;
+        }
+    }
+    // verification output: ascending ids of the selected nodes of the tile
+    if (sel_ids) {
+        __shared__ unsigned s_pre[SEL_WORDS];
+        static_assert(SEL_WORDS == 32 * 8, "warp 0 scans 8 words per lane");
+        if (warp == 0) {
+            unsigned c8[8], sum = 0;
+#pragma unroll
+            for (int j = 0; j < 8; j++) {
+                c8[j] = __popc(s_selw[8 * lane + j]);
+                sum += c8[j];
+            }
+            unsigned incl = sum;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned y = __shfl_up_sync(FULL, incl, o);
+                if (lane >= o) incl += y;
+            }
+            unsigned run = incl - sum;
+#pragma unroll
+            for (int j = 0; j < 8; j++) {
+                s_pre[8 * lane + j] = run;
+                run += c8[j];
+            }
+        }
+        __syncthreads();
+        const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+        for (int k = 0; k < 2 * R; k++) {
+            const int wt = 32 * (k >> 1) + 2 * warp + (k & 1);
+            const unsigned sw = s_selw[wt];
+            if ((sw >> lane) & 1u)
+                sel_ids[t0 + s_pre[wt] + __popc(sw & lt)] = (int32_t)(t0 + 32 * wt + lane);
+        }
     }
 }
 
@@ -611,17 +684,78 @@ template <typename T, bool SUB>
 __global__ void __launch_bounds__(SEL_THREADS)
     k_plan(T *Ft, T *Fd, double *Hs, const GraphPtrs *__restrict__ gp, const double *__restrict__ dscale,
            int64_t n, int64_t ntiles, const unsigned *tile_cnt, const unsigned *tile_diff, const float *tile_l1f,
-           const unsigned *tile_maxf, const unsigned *tile_maxu, DevCtl *ctl, int use_cond,
-           cudaGraphConditionalHandle cond, unsigned long long *stats)
+           const unsigned *tile_maxf, const unsigned *tile_maxu, const uint64_t *__restrict__ hub_base,
+           const unsigned *__restrict__ tile_hub, DevCtl *ctl, int use_cond, cudaGraphConditionalHandle cond,
+           unsigned long long *stats)
 {
     typedef typename FluidWord<T>::U U;
     constexpr int NW = SEL_THREADS / 32;
     __shared__ unsigned long long s_red[4][NW];
     __shared__ float s_l1[NW];
     __shared__ unsigned s_go;
-    volatile DevCtl *vc = ctl;
-    if (vc->done) return;   // the selection has already closed the loop
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const Off *__restrict__ rp = gp->rp;
+    const unsigned *__restrict__ hub_list = gp->hub_list;
+    const uint64_t hub_cap = gp->hub_cap;
+    const unsigned long long stream = pol_first(), keep = pol_last();
+    // Warps over the tiles, lanes over a tile's selected hubs (32 at a time).
+    // The first round of each warp is requested before the control block and
+    // the tile partials, so its three dependent loads (count, id, node data)
+    // overlap the reduction; every index is clamped to its array, so a list
+    // left by an earlier sweep (the selection of this one returned early) is
+    // read harmlessly and then not used.
+    // control fields, requested at once (volatile loads would be issued one
+    // after another); only the selection, the previous plan and the previous
+    // push wrote them, all finished
+    const unsigned done0 = __ldcg(&ctl->done);
+    int c_inf = 0;
+    unsigned long long c_sweep = 0, c_max_sweeps = 0, c_links = 0, c_pushes = 0, c_diff = 0;
+    double c_stop = 0.0, c_d = 0.0, c_tf = 0.0, c_cap = 0.0;
+    if (threadIdx.x == 0) {
+        c_inf = __ldcg(&ctl->inf_norm);
+        c_sweep = __ldcg(&ctl->sweep);
+        c_max_sweeps = __ldcg(&ctl->max_sweeps);
+        c_stop = __ldcg(&ctl->sweep_stop);
+        if (blockIdx.x == 0) {
+            c_links = __ldcg(&ctl->sweep_links);
+            c_pushes = __ldcg(&ctl->edge_pushes);
+            c_diff = __ldcg(&ctl->diffusions);
+            c_d = __ldcg(&ctl->d);
+            c_tf = __ldcg(&ctl->theta_factor);
+            c_cap = __ldcg(&ctl->inf_cap);
+        }
+    }
+    const int64_t gw = ((int64_t)blockIdx.x * SEL_THREADS + threadIdx.x) >> 5;
+    const int64_t nwarps = (int64_t)gridDim.x * (SEL_THREADS / 32);
+    struct HubTake {
+        unsigned i;
+        U fbits;
+        Off r0, r1;
+        unsigned long long hb;
+        double ds;
+    };
+    auto load_hub = [&](int64_t tw, unsigned h, unsigned nt, HubTake &t) -> bool {
+        if (h >= nt) return false;
+        const uint64_t q = __ldg(hub_base + tw) + h;
+        if (q >= hub_cap) return false;
+        t.i = hub_list[q];
+        if (t.i >= (uint64_t)n) return false;
+        t.fbits = ld_word(Ft + t.i, keep);
+        t.r0 = ldnc_u32(rp + t.i, stream);
+        t.r1 = ldnc_u32(rp + t.i + 1, stream);
+        t.hb = ld_b64(Hs + t.i, stream);
+        t.ds = ldnc_f64(dscale + t.i, stream);
+        return true;
+    };
+    unsigned nt0 = 0;
+    HubTake first = {};
+    bool have_first = false;
+    if (gw < ntiles) {
+        nt0 = __ldg(tile_hub + gw);
+        have_first = load_hub(gw, lane, nt0, first);
+    }
+    volatile DevCtl *vc = ctl;
+    if (done0) return;   // the selection has already closed the loop
     // fixed order: thread-strided tiles, xor butterfly, warps in order; every
     // partial rounded upward, so every CTA gets the same upper bound
     float sfx = 0.0f;
@@ -663,18 +797,18 @@ __global__ void __launch_bounds__(SEL_THREADS)
             mu = s_red[3][w] > mu ? s_red[3][w] : mu;
         }
         const double sa = (double)sfx;
-        const bool inf_norm = vc->inf_norm != 0;
-        const unsigned long long sweep = vc->sweep;
+        const bool inf_norm = c_inf != 0;
+        const unsigned long long sweep = c_sweep;
         unsigned done = 0;
         // every |F_i| and every partial sum was rounded up: an upper bound of
         // |F_t|_1 (or of max |F_i| in the infinity-norm mode)
-        if ((inf_norm ? (double)__uint_as_float((unsigned)mu) : sa) <= vc->sweep_stop) done = 1;
-        else if (sweep >= vc->max_sweeps) done = 2;
+        if ((inf_norm ? (double)__uint_as_float((unsigned)mu) : sa) <= c_stop) done = 1;
+        else if (sweep >= c_max_sweeps) done = 2;
         s_go = done == 0;
         if (blockIdx.x == 0) {
             // fold the links of the previous push into the totals
-            const unsigned long long links = vc->sweep_links;
-            vc->edge_pushes = vc->edge_pushes + links;
+            const unsigned long long links = c_links;
+            vc->edge_pushes = c_pushes + links;
             if (stats && sweep >= 1 && sweep <= (unsigned long long)STAT_CAP) stats[2 * (sweep - 1)] = links;
             vc->sweep_links = 0;
             vc->l1 = sa;
@@ -689,15 +823,15 @@ __global__ void __launch_bounds__(SEL_THREADS)
             // max |F| / (1 - d) during the sweep and V = d max |F| / (1 - d).
             // (The refinement pass takes each node once: V = d |D|_1 < sa.)
             {
-                const double hop = vc->d / (1.0 - vc->d);
+                const double hop = c_d / (1.0 - c_d);
                 const double base = inf_norm ? (double)__uint_as_float((unsigned)mu) : sa;
                 vc->hot_scale = base * fmax(inf_norm ? 8.0 : 1.0, 0.125 * hop);
             }
             if (!done) {
-                vc->diffusions = vc->diffusions + sd;
+                vc->diffusions = c_diff + sd;
                 vc->nent = sc;
                 if (stats && sweep < (unsigned long long)STAT_CAP) stats[2 * sweep + 1] = sc;
-                double th = vc->theta_factor * sa / (double)n;
+                double th = c_tf * sa / (double)n;
                 // A sweep that took nothing leaves F unchanged; the largest |F_i|
                 // passes the DI-argmax test exactly, so never ask for more than
                 // that (this covers a rounded average above several equal fluids).
@@ -705,64 +839,58 @@ __global__ void __launch_bounds__(SEL_THREADS)
                 if (sd == 0 && fmax < th) th = fmax;
                 // infinity-norm mode: theta <= inf_cap max |F_i| with inf_cap + d < 1,
                 // so max |F| shrinks by at least inf_cap + d per sweep
-                if (inf_norm && vc->inf_cap * fmax < th) th = vc->inf_cap * fmax;
+                if (inf_norm && c_cap * fmax < th) th = c_cap * fmax;
                 vc->theta = th;
             }
             vc->push_ready = done ? 0u : 1u;
-            __threadfence();
-            vc->done = done;
+            vc->done = done;   // read by the next kernels only (kernel order makes it visible)
             if (use_cond) cudaGraphSetConditional(cond, done ? 0u : 1u);
         }
     }
     __syncthreads();
     if (!s_go) return;
-    // take the selected hubs: one thread each
-    const Off *__restrict__ rp = gp->rp;
-    const unsigned *__restrict__ hub_list = gp->hub_list;
+    // take the selected hubs (no push is running: F is quiescent), one lane
+    // each, and cut their rows into pieces; one piece-queue reservation per
+    // warp and round
     Off *pc_row = gp->pc_row, *pc_len = gp->pc_len;
     double *pc_val = gp->pc_val;
     const Off piece = gp->piece;
-    const unsigned long long nhub = vc->nhub;
-    const unsigned long long stream = pol_first(), keep = pol_last();
-    // warps over 32 consecutive list entries; one piece-queue reservation per warp
-    for (unsigned long long h0 = ((unsigned long long)blockIdx.x * SEL_THREADS + threadIdx.x) & ~31ull; h0 < nhub;
-         h0 += (unsigned long long)gridDim.x * SEL_THREADS) {
-        const unsigned long long h = h0 + lane;
-        unsigned np = 0;
-        Off r0 = 0, deg = 0;
-        double v = 0.0;
-        if (h < nhub) {
-            const unsigned i = hub_list[h];
-            const U fbits = ld_word(Ft + i, keep);
-            r0 = ldnc_u32(rp + i, stream);
-            const Off r1 = ldnc_u32(rp + i + 1, stream);
-            const unsigned long long hb = ld_b64(Hs + i, stream);
-            const double ds = ldnc_f64(dscale + i, stream);
-            const double f = (double)word_val(fbits);
-            st_b64(Hs + i, (unsigned long long)__double_as_longlong(__longlong_as_double((long long)hb) + f),
-                   stream);
-            st_word(Ft + i, (U)0, keep);
-            if (SUB) red_add_f64(reinterpret_cast<double *>(Fd) + i, -f, keep);
-            deg = r1 - r0;
-            v = f * ds;
-            np = (deg + piece - 1) / piece;
-        }
-        unsigned incl = np;
+    for (int64_t tw = gw; tw < ntiles; tw += nwarps) {
+        const unsigned nt = tw == gw ? nt0 : __ldg(tile_hub + tw);
+        for (unsigned h0 = 0; h0 < nt; h0 += 32) {
+            HubTake t = {};
+            const bool mine = (tw == gw && h0 == 0) ? have_first : load_hub(tw, h0 + lane, nt, t);
+            if (tw == gw && h0 == 0) t = first;
+            unsigned np = 0;
+            Off deg = 0;
+            double v = 0.0;
+            if (mine) {
+                const double f = (double)word_val(t.fbits);
+                st_b64(Hs + t.i, (unsigned long long)__double_as_longlong(__longlong_as_double((long long)t.hb) + f),
+                       stream);
+                st_word(Ft + t.i, (U)0, keep);
+                if (SUB) red_add_f64(reinterpret_cast<double *>(Fd) + t.i, -f, keep);
+                deg = t.r1 - t.r0;
+                v = f * t.ds;
+                np = (deg + piece - 1) / piece;
+            }
+            unsigned incl = np;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const unsigned y = __shfl_up_sync(FULL, incl, o);
-            if (lane >= o) incl += y;
-        }
-        const unsigned wtot = __shfl_sync(FULL, incl, 31);
-        unsigned long long wbase = 0;
-        if (lane == 31 && wtot) wbase = atomicAdd((unsigned long long *)&ctl->npieces, (unsigned long long)wtot);
-        wbase = __shfl_sync(FULL, wbase, 31);
-        unsigned long long pb = wbase + incl - np;
-        for (Off o = 0; o < deg; o += piece) {
-            pc_row[pb] = r0 + o;
-            pc_len[pb] = deg - o < piece ? deg - o : piece;
-            pc_val[pb] = v;
-            pb++;
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned y = __shfl_up_sync(FULL, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const unsigned wtot = __shfl_sync(FULL, incl, 31);
+            unsigned long long wbase = 0;
+            if (lane == 31 && wtot) wbase = atomicAdd((unsigned long long *)&ctl->npieces, (unsigned long long)wtot);
+            wbase = __shfl_sync(FULL, wbase, 31);
+            unsigned long long pb = wbase + incl - np;
+            for (Off o = 0; o < deg; o += piece) {
+                pc_row[pb] = t.r0 + o;
+                pc_len[pb] = deg - o < piece ? deg - o : piece;
+                pc_val[pb] = v;
+                pb++;
+            }
         }
     }
 }
@@ -819,6 +947,7 @@ __device__ __forceinline__ float link_weight(const float *w32, Off link, unsigne
 __device__ __forceinline__ bool hot_add(unsigned long long *s_hot, int slot, double v, int hot_shift)
 {
     const int ex = (int)(((unsigned long long)__double_as_longlong(v) >> 52) & 0x7ffu);
+    if (ex == 0) return v == 0.0;   // a subnormal contribution goes to global memory as it is
     if (ex - 1023 + hot_shift > 58) return false;
     atomicAdd(s_hot + slot, (unsigned long long)to_fixed64(v, hot_shift));
     return true;
@@ -914,22 +1043,25 @@ __global__ void __launch_bounds__(PUSH_THREADS, 4)
     __shared__ unsigned s_start[PUSH_THREADS / 32][32 * 4];
     __shared__ Off s_row[PUSH_THREADS / 32][32 * 4];
     __shared__ T s_val[PUSH_THREADS / 32][32 * 4];
+    // control fields, requested at once (the plan that wrote them is over)
+    const unsigned ready = __ldcg(&ctl->push_ready);
+    const double hot_scale = __ldcg(&ctl->hot_scale);
+    const unsigned long long npieces0 = __ldcg(&ctl->npieces);
     volatile DevCtl *vc = ctl;
-    if (!vc->push_ready) return;
+    if (!ready) return;
     // 8 hot_scale bounds what this sweep adds into one page, for every d
     // (k_plan derives it): with 2^(e-1) <= hot_scale < 2^e, units of
     // 2^(e - 58) keep every slot below 2^61.
     int e = 0;
-    frexp(vc->hot_scale, &e);
+    frexp(hot_scale, &e);
     const int hot_shift = 58 - e;
     for (int k = threadIdx.x; k < nhot; k += PUSH_THREADS) s_hot[k] = 0ull;
     __syncthreads();
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        vc->nhub = 0;                 // the plan has consumed the hub list
         vc->sweep = vc->sweep + 1;    // (the plan reads it; it is stable until here)
     }
     // unit and piece counts stay below 2^32 (n / 128 units; pieces <= links)
-    const unsigned npc = (unsigned)vc->npieces;
+    const unsigned npc = (unsigned)npieces0;
     const unsigned long long keep = pol_last(), stream = pol_first();
     const int lane = threadIdx.x & 31;
     const unsigned nunits = (unsigned)(ngroups / Q);
@@ -1051,9 +1183,10 @@ __global__ void __launch_bounds__(PUSH_THREADS, 4)
 }
 
 // Static hub bit mask: node i has more than hub_deg out-links.
-// One node per thread, one word per warp (ballot); the grid covers whole words.
+// One node per thread, one word per warp (ballot); the grid covers whole
+// words.  tile_hubs[t] counts the hub nodes of selection tile t.
 __global__ void k_hubbits(const Off *rp, int64_t n, int64_t words, Off hub_deg, unsigned *hubbits,
-                          unsigned long long *count)
+                          unsigned *tile_hubs, unsigned long long *count)
 {
     unsigned long long c = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < words * 32;
@@ -1063,6 +1196,7 @@ __global__ void k_hubbits(const Off *rp, int64_t n, int64_t words, Off hub_deg, 
         if ((threadIdx.x & 31) == 0) {
             hubbits[i >> 5] = word;
             c += __popc(word);
+            if (word) atomicAdd(tile_hubs + i / TILE, (unsigned)__popc(word));
         }
     }
     if (c) atomicAdd(count, c);
@@ -1105,11 +1239,16 @@ di_status state_prepare_graph(di_graph_s *g, di_state_s *st, cudaStream_t s)
     const int64_t words = st->ntiles * TILE / 32;
     Temps t(s);
     unsigned long long *cnt;
+    unsigned *tile_hubs;
     DI_TRY(t.get(&cnt, 1));
+    DI_TRY(t.get(&tile_hubs, st->ntiles));
     DI_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), s));
+    DI_CUDA(cudaMemsetAsync(tile_hubs, 0, sizeof(unsigned) * st->ntiles, s));
     k_hubbits<<<grid_for(words * 32, 256), 256, 0, s>>>(static_cast<const Off *>(g->rp), g->n, words,
-                                                   (Off)st->hub_deg, st->hubbits, cnt);
+                                                   (Off)st->hub_deg, st->hubbits, tile_hubs, cnt);
     count_launches(1);
+    // each tile lists its selected hubs in a region of its own
+    DI_TRY(scan_exclusive<uint32_t>(tile_hubs, st->hub_base, st->ntiles, nullptr, s));
     DI_CUDA(cudaGetLastError());
     unsigned long long nh = 0;
     DI_CUDA(cudaMemcpyAsync(&nh, cnt, sizeof(nh), cudaMemcpyDeviceToHost, s));
@@ -1156,6 +1295,7 @@ di_status state_sync_ptrs(di_graph_s *g, di_state_s *st, cudaStream_t s)
     h->w = g->w;
     h->w32 = g->w32;
     h->hub_list = st->hub_list;
+    h->hub_cap = (uint64_t)st->nhub_cap;
     h->pc_row = st->pc_row;
     h->pc_len = st->pc_len;
     h->pc_val = st->pc_val;
@@ -1178,6 +1318,8 @@ di_status state_alloc(di_state_s *st, cudaStream_t s)
     DI_TRY(dalloc_t(&st->mask, slots / 32, s));
     DI_TRY(dalloc_t(&st->hubbits, slots / 32, s));
     DI_TRY(dalloc_t(&st->tile_cnt, st->ntiles, s));
+    DI_TRY(dalloc_t(&st->tile_hub, st->ntiles, s));
+    DI_TRY(dalloc_t(&st->hub_base, st->ntiles, s));
     DI_TRY(dalloc_t(&st->tile_diff, st->ntiles, s));
     DI_TRY(dalloc_t(&st->tile_l1f, st->ntiles, s));
     DI_TRY(dalloc_t(&st->tile_maxf, st->ntiles, s));
@@ -1209,7 +1351,7 @@ di_status state_free(di_state_s *st)
     if (st->gexec) cudaGraphExecDestroy(st->gexec);
     if (st->gexec32) cudaGraphExecDestroy(st->gexec32);
     if (st->gstream) cudaStreamDestroy(st->gstream);
-    void *bufs[] = {st->F, st->H, st->dscale, st->dtab, st->mask, st->hubbits, st->hub_list, st->pc_row, st->pc_len,
+    void *bufs[] = {st->F, st->H, st->dscale, st->dtab, st->tile_hub, st->hub_base, st->mask, st->hubbits, st->hub_list, st->pc_row, st->pc_len,
                     st->pc_val, st->tile_cnt, st->tile_diff, st->tile_l1f, st->tile_maxf, st->tile_l1,
                     st->tile_l, st->ctl, st->stats, st->F32, st->D, st->rctl, st->tile_maxu, st->tile_max,
                     st->gp};
@@ -1249,11 +1391,11 @@ static void launch_select(di_graph_s *g, di_state_s *st, const Sweep &w, cudaStr
 {
     if (w.kind == SW_F32)
         k_select<float><<<(unsigned)st->ntiles, SEL_THREADS, 0, s>>>(
-            static_cast<const float *>(w.Ft), g->n, st->mask, st->hubbits, st->gp, st->tile_cnt,
+            static_cast<const float *>(w.Ft), g->n, st->mask, st->hubbits, st->gp, st->hub_base, st->tile_hub, st->tile_cnt,
             st->tile_diff, st->tile_l1f, st->tile_maxf, st->tile_maxu, w.ctl, use_cond, h, sel_ids);
     else
         k_select<double><<<(unsigned)st->ntiles, SEL_THREADS, 0, s>>>(
-            static_cast<const double *>(w.Ft), g->n, st->mask, st->hubbits, st->gp, st->tile_cnt,
+            static_cast<const double *>(w.Ft), g->n, st->mask, st->hubbits, st->gp, st->hub_base, st->tile_hub, st->tile_cnt,
             st->tile_diff, st->tile_l1f, st->tile_maxf, st->tile_maxu, w.ctl, use_cond, h, sel_ids);
     count_launches(1);
 }
@@ -1264,7 +1406,7 @@ static void launch_plan(di_graph_s *g, di_state_s *st, const Sweep &w, cudaStrea
     unsigned long long *stats = w.kind == SW_REFINE ? nullptr : st->stats;
 #define DI_PLAN_ARGS                                                                                   \
     w.Hs, st->gp, st->dscale, g->n, st->ntiles, st->tile_cnt, st->tile_diff, st->tile_l1f, st->tile_maxf, \
-        st->tile_maxu, w.ctl, use_cond, h, stats
+        st->tile_maxu, st->hub_base, st->tile_hub, w.ctl, use_cond, h, stats
     if (w.kind == SW_F32)
         k_plan<float, false><<<PLAN_CTAS, SEL_THREADS, 0, s>>>(static_cast<float *>(w.Ft),
                                                                static_cast<float *>(w.Fd), DI_PLAN_ARGS);

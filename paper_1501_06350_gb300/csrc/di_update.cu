@@ -6,7 +6,8 @@
 // last operation on a link decides).  Each distinct batch link is looked up
 // in its (sorted) old row and classified: inserted, deleted, re-weighted or
 // no-op.  Rows without an effective change are moved as they are (a warp per
-// 32 rows, coalesced); the changed rows are merged with their batch entries.
+// 32 rows, coalesced); in the changed rows every kept old link and every
+// inserted link computes its own position from prefix counts (no serial merge).
 // A source j is "touched" when its set of out-links or a weight changes, i.e.
 // when column j of P changes; only those columns contribute to d (P' - P) H,
 // and for them the whole old column is withdrawn and the whole new column
@@ -217,7 +218,7 @@ __global__ void k_chunk_fill(const uint32_t *cnt, const uint64_t *cpos, const ui
     }
 }
 
-// First batch entry of row j whose target is >= t, inside [q, qe).
+// First batch entry of row j whose target is >= key's, inside [q, qe).
 __device__ __forceinline__ int64_t lower_target(const uint64_t *ukey, int64_t q, int64_t qe, uint64_t key)
 {
     while (q < qe) {
@@ -228,73 +229,79 @@ __device__ __forceinline__ int64_t lower_target(const uint64_t *ukey, int64_t q,
     return q;
 }
 
-// One chunk of a changed row: its old links [c CH, (c+1) CH) merged with the
-// row's batch entries whose targets fall in the chunk's target range (from
-// the chunk's first target up to the next chunk's first target; the first
-// and last chunks are open-ended).  The output position of the chunk's first
-// element is its old position minus the deletions and plus the insertions
-// listed before it (ins_pre / del_pre: exclusive prefix counts over the
-// sorted batch).
-__global__ void k_merge_chunks(const uint32_t *ch_row, const uint32_t *ch_idx, const uint64_t *nch_dev,
-                               const uint32_t *tlist, const uint32_t *qs, const uint32_t *qes, const Off *rp,
-                               const int32_t *col, const double *w, const int32_t *pcol, const int *slot_of,
-                               const Off *nrp, const uint64_t *ukey, const uint8_t *eff, const double *uw,
-                               const uint64_t *ins_pre, const uint64_t *del_pre, int32_t *ncol, double *nw,
-                               int32_t *npcol)
+// The merged row j of the new CSR holds, in target order, the old links not
+// deleted and the inserted ones.  An old link at position i (target c) lands
+// at nrp[j] + (i - rp[j]) - (deletions with target < c) + (insertions with
+// target < c); the batch entries of the row are sorted by target, so both
+// counts are prefix differences (ins_pre / del_pre: exclusive counts over the
+// sorted batch) at the row's first entry with target >= c.  One warp per
+// chunk of CH old links, one lane per link.
+__global__ void k_merge_old(const uint32_t *ch_row, const uint32_t *ch_idx, const uint64_t *nch_dev,
+                            const uint32_t *tlist, const uint32_t *qs, const uint32_t *qes, const Off *rp,
+                            const int32_t *col, const double *w, const int32_t *pcol, const Off *nrp,
+                            const uint64_t *ukey, const uint8_t *eff, const double *uw, const uint64_t *ins_pre,
+                            const uint64_t *del_pre, int32_t *ncol, double *nw, int32_t *npcol)
 {
     const int64_t nch = (int64_t)*nch_dev;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nch;
-         t += (int64_t)gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < nch; t += nwarp) {
         const uint32_t r = ch_row[t];
         const uint32_t j = tlist[r];
-        const Off c = ch_idx[t];
         const Off a = rp[j], b = rp[j + 1];
-        const int64_t q = qs[r];
-        const int64_t qe = qes[r];
-        const Off i0 = a + c * CH;
-        const Off i1 = (b - i0 > CH) ? i0 + CH : b;
+        const Off i0 = a + ch_idx[t] * CH;
+        const Off i1 = (b > i0 && b - i0 > CH) ? i0 + CH : b;
+        const int64_t q = qs[r], qe = qes[r];
         const uint64_t rowkey = (uint64_t)j << 32;
-        const int64_t q0 = c == 0 ? q : lower_target(ukey, q, qe, rowkey | (uint32_t)col[i0]);
-        const int64_t q1 = i1 == b ? qe : lower_target(ukey, q, qe, rowkey | (uint32_t)col[i1]);
-        Off out = nrp[j] + (i0 - a) - (Off)(del_pre[q0] - del_pre[q]) + (Off)(ins_pre[q0] - ins_pre[q]);
-        Off i = i0;
-        int64_t k = q0;
-        while (i < i1 || k < q1) {
-            const int64_t to = i < i1 ? (int64_t)col[i] : INT64_MAX;
-            const int64_t tb = k < q1 ? (int64_t)(uint32_t)ukey[k] : INT64_MAX;
-            int32_t cc = -1, pc = 0;
-            double x = 1.0;
-            if (to < tb) {
-                cc = (int32_t)to;
-                x = w ? w[i] : 1.0;
-                if (npcol) pc = pcol[i];
-                i++;
-            } else if (to == tb) {
-                const unsigned char e = eff[k];
-                if (e != EFF_DEL) {
-                    cc = (int32_t)to;
-                    x = e == EFF_UPD ? uw[k] : (w ? w[i] : 1.0);
-                    if (npcol) pc = pcol[i];
-                }
-                i++;
-                k++;
-            } else {
-                if (eff[k] == EFF_INS) {
-                    cc = (int32_t)tb;
-                    x = uw[k];
-                    if (npcol) {
-                        const int sl = slot_of[cc];
-                        pc = sl >= 0 ? (int32_t)(0x80000000u | (unsigned)sl) : cc;
-                    }
-                }
-                k++;
-            }
-            if (cc >= 0) {
-                ncol[out] = cc;
-                if (nw) nw[out] = x;
-                if (npcol) npcol[out] = pc;
-                out++;
-            }
+        const Off out0 = nrp[j] - a;
+        for (Off i = i0 + lane; i < i1; i += 32) {
+            const int32_t c = col[i];
+            const int64_t k = lower_target(ukey, q, qe, rowkey | (uint32_t)c);
+            unsigned char e = EFF_NOP;
+            if (k < qe && (uint32_t)ukey[k] == (uint32_t)c) e = eff[k];
+            if (e == EFF_DEL) continue;
+            const Off out = out0 + i - (Off)(del_pre[k] - del_pre[q]) + (Off)(ins_pre[k] - ins_pre[q]);
+            ncol[out] = c;
+            if (nw) nw[out] = e == EFF_UPD ? uw[k] : w[i];
+            if (npcol) npcol[out] = pcol[i];
+        }
+    }
+}
+
+// First position in the old row [a, b) whose target is >= c.
+__device__ __forceinline__ Off lower_col(const int32_t *col, Off a, Off b, int32_t c)
+{
+    while (a < b) {
+        const Off mid = a + ((b - a) >> 1);
+        if (col[mid] < c) a = mid + 1;
+        else b = mid;
+    }
+    return a;
+}
+
+// An inserted link (batch entry k of row j, target c) lands at nrp[j] + (old
+// links with target < c) - (deletions before it) + (insertions before it).
+// One thread per distinct batch entry.
+__global__ void k_merge_ins(const uint64_t *ukey, const uint64_t *nu_dev, const uint8_t *eff, const double *uw,
+                            const uint64_t *ins_pre, const uint64_t *del_pre, const uint64_t *tpos, const uint32_t *qs,
+                            const Off *rp, const int32_t *col, const int *slot_of, const Off *nrp, int32_t *ncol,
+                            double *nw, int32_t *npcol)
+{
+    const int64_t nu = (int64_t)*nu_dev;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nu;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        if (eff[k] != EFF_INS) continue;
+        const uint32_t j = (uint32_t)(ukey[k] >> 32);
+        const int32_t c = (int32_t)(uint32_t)ukey[k];
+        const int64_t q = qs[tpos[j]];
+        const Off a = rp[j];
+        const Off ob = lower_col(col, a, rp[j + 1], c);
+        const Off out = nrp[j] + (ob - a) - (Off)(del_pre[k] - del_pre[q]) + (Off)(ins_pre[k] - ins_pre[q]);
+        ncol[out] = c;
+        if (nw) nw[out] = uw[k];
+        if (npcol) {
+            const int sl = slot_of[c];
+            npcol[out] = sl >= 0 ? (int32_t)(0x80000000u | (unsigned)sl) : c;
         }
     }
 }
@@ -330,8 +337,10 @@ __global__ void k_flags(const uint8_t *eff, const uint64_t *nu_dev, uint8_t *ins
     }
 }
 
-// F += sign * d H_j P[:, j] for the listed columns, one warp per chunk of CH
-// links of a column.
+// F += sign * d H_j P[:, j] for the listed columns (chunks of at most CH
+// links), one warp per chunk: lane 0 computes the column's share (one FP64
+// division per chunk), and the lanes add it along the chunk's links, four
+// links each in flight (their targets loaded before the adds).
 __global__ void k_inject_chunks(const uint32_t *ch_row, const uint32_t *ch_idx, const uint64_t *nch_dev,
                                 const uint32_t *tlist, const Off *rp, const int32_t *col, const double *w,
                                 const double *wsum, const double *H, double sd, double *F)
@@ -345,15 +354,25 @@ __global__ void k_inject_chunks(const uint32_t *ch_row, const uint32_t *ch_idx, 
         const Off i0 = a + ch_idx[t] * CH;
         if (i0 >= b) continue;
         const Off i1 = (b - i0 > CH) ? i0 + CH : b;
-        // one FP64 division per chunk (lane 0), not one per lane: FP64 issue
-        // is scarce on this part
         double unit = 0.0;
         if (lane == 0) {
             const double h = sd * H[j];
             unit = w ? h / wsum[j] : h / (double)(b - a);
         }
         unit = __shfl_sync(FULL, unit, 0);
-        for (Off e = i0 + lane; e < i1; e += 32) atomicAdd(F + col[e], w ? unit * w[e] : unit);
+        for (Off base = i0; base < i1; base += 128) {
+            int32_t c[4];
+            double v[4];
+#pragma unroll
+            for (int g = 0; g < 4; g++) {
+                const Off e = base + g * 32 + lane;
+                c[g] = e < i1 ? col[e] : -1;
+                v[g] = (e < i1 && w) ? unit * w[e] : unit;
+            }
+#pragma unroll
+            for (int g = 0; g < 4; g++)
+                if (c[g] >= 0) atomicAdd(F + c[g], v[g]);
+        }
     }
 }
 
@@ -405,7 +424,9 @@ di_status update_edges(di_graph_s *g, di_state_s *st, int64_t m, const int32_t *
     // on the device: the arrays are sized by their bounds and the kernels
     // that depend on a count read it there, so the whole update runs without
     // a host round trip until the new link count is read at the end.
-    const unsigned pgrid = (unsigned)(8 * sm_count(g->device));   // grid of the count-driven kernels
+    // grids of the count-driven kernels: one full wave (2048 threads per SM)
+    const unsigned pgrid = (unsigned)(8 * sm_count(g->device));    // 256-thread blocks
+    const unsigned pgrid128 = 2 * pgrid;                           // 128-thread blocks
     uint64_t *nu_dev, *mnew_dev, *nt_dev, *och_dev, *nch_dev;
     DI_TRY(t.get(&nu_dev, 1));
     DI_TRY(t.get(&mnew_dev, 1));
@@ -516,10 +537,12 @@ di_status update_edges(di_graph_s *g, di_state_s *st, int64_t m, const int32_t *
     k_chunk_fill<<<pgrid, 256, 0, s>>>(ocnt, ocpos, nt_dev, och_row, och_idx);
     k_chunk_fill<<<pgrid, 256, 0, s>>>(ncnt, ncpos, nt_dev, nch_row, nch_idx);
     count_launches(2);
-    k_merge_chunks<<<pgrid, 128, 0, s>>>(och_row, och_idx, och_dev, tlist, qs, qe, rp, g->col, g->w, g->pcol,
-                                         g->slot_of, nrp, ukey, eff, uw, ins_pre, del_pre, ncol, nwv, npcol);
-    count_launches(1);
-    k_row_finish<<<pgrid, 128, 0, s>>>(tlist, nt_dev, rp, nrp, nwv, nwsum, ddang);
+    k_merge_old<<<pgrid, 256, 0, s>>>(och_row, och_idx, och_dev, tlist, qs, qe, rp, g->col, g->w, g->pcol, nrp, ukey,
+                                      eff, uw, ins_pre, del_pre, ncol, nwv, npcol);
+    k_merge_ins<<<pgrid, 256, 0, s>>>(ukey, nu_dev, eff, uw, ins_pre, del_pre, tpos, qs, rp, g->col, g->slot_of, nrp,
+                                      ncol, nwv, npcol);
+    count_launches(2);
+    k_row_finish<<<pgrid128, 128, 0, s>>>(tlist, nt_dev, rp, nrp, nwv, nwsum, ddang);
     count_launches(1);
     // 6. F += d (P' - P) H: withdraw the old columns, inject the new ones
     if (st) {
