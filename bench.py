@@ -144,6 +144,19 @@ def run_reference(args, g):
             "e2e": {"value": val, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def atomic_ceiling(torch):
+    """Throughput of FP64 atomic additions at random slots of an L2-resident
+    32 MB vector (the push adds into its 32 MB fluid at random pages), measured
+    live by the library's probe (di_probe_atomic_adds): the ceiling of an
+    atomic-bound scatter on this GPU."""
+    from paper_1501_06350_gb300 import _lib
+    g = ctypes.c_double(0.0)
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    _lib.check(_lib.lib().di_probe_atomic_adds(torch.cuda.current_device(), ctypes.byref(g), stream),
+               "di_probe_atomic_adds")
+    return g.value
+
+
 def update_bytes(cp, n, src, op):
     """Algorithmic bytes of one link batch applied by Section 3.5 (Theorem
     update): the batch read (source, target, op: 9 B per change), the CSR
@@ -482,6 +495,12 @@ def main():
                     help="run only the dynamic update on the 50M-page / ~600M-link graph and print it")
     ap.add_argument("--batch-only", action="store_true",
                     help="run only the batched leg (for profiling) and print it as the JSON line")
+    ap.add_argument("--profile-solve", action="store_true",
+                    help="profiling aid: one warm from-scratch solve, then one eager solve inside the NVTX "
+                         "range 'profiled' (options from --theta/--hub-deg/--piece/--precision); prints the "
+                         "push statistics of that solve")
+    ap.add_argument("--hub-deg", type=int, default=None, help="degree-bin threshold (default: library default)")
+    ap.add_argument("--piece", type=int, default=None, help="links per hub piece (default: library default)")
     args = ap.parse_args()
     if args.warmup < 3 and not args.small:
         ap.error("--warmup must be >= 3")
@@ -504,6 +523,8 @@ def main():
         from paper_1501_06350_gb300 import di as di_mod
         print(json.dumps({"update50m": update50m_leg(torch, di_mod)}), flush=True)
         return 0
+    if args.profile_solve:
+        return profile_solve(args, torch)
     if args.batch_only:
         from paper_1501_06350_gb300 import di as di_mod
         pk = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
@@ -541,6 +562,10 @@ def main():
                   "default_ms": trep["default_ms"], "trials": trep["trials"]}
     if args.theta is not None:
         sopt["theta_factor"] = args.theta
+    if args.hub_deg is not None:
+        sopt["hub_deg"] = args.hub_deg
+    if args.piece is not None:
+        sopt["piece"] = args.piece
 
     def step():
         H, i1 = st.solve(D, tol=TOL, use_graph=ug, **sopt)
@@ -611,9 +636,21 @@ def main():
     achieved = alg_bytes / push_avg_s / 1e9
     run_opts = {"theta_factor": sopt.get("theta_factor", 1.0), "hub_deg": sopt.get("hub_deg", 256),
                 "piece": sopt.get("piece", 1024)}
-    traffic = traffic_for(f"push_web4m_{args.precision}_c{run_opts['theta_factor']:g}_traffic.json", run_opts)
+    traffic = traffic_for(f"push_web4m_{args.precision}_c{run_opts['theta_factor']:g}_h{run_opts['hub_deg']}"
+                          f"_p{run_opts['piece']}_traffic.json", run_opts)
+    # the push's binding limit on this GPU is the L2's throughput of atomic
+    # additions, not HBM: per launch, one exchange and one history add per
+    # taken node and one add per link whose target is not a hot page (hot
+    # pages are summed in shared memory; their one add per CTA is not counted)
+    hot_per_launch = prof.get("push_hot_links", 0) / max(prof["push_launches"], 1)
+    atomic_ops = per_launch_links - hot_per_launch + 2.0 * per_launch_nodes
+    ceiling = atomic_ceiling(torch)
+    atomics = {"bound": "l2_atomics", "achieved": atomic_ops / push_avg_s / 1e9, "peak": ceiling,
+               "unit": "G atomic ops/s", "frac": atomic_ops / push_avg_s / 1e9 / ceiling,
+               "ops_per_launch": atomic_ops, "hot_link_share": hot_per_launch / max(per_launch_links, 1.0),
+               "peak_source": "measured live: di_probe_atomic_adds, 32M FP64 atomic adds at random slots of a 32 MB vector"}
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic,
+                "frac": achieved / peak, "traffic": traffic, "l2_atomics": atomics,
                 "kernel": "k_push<float>" if args.precision == "f32" else "k_push<double>",
                 "bytes_per_link": link_bytes, "bytes_per_node": node_bytes,
                 "nodes_per_launch": per_launch_nodes,
@@ -661,6 +698,39 @@ def main():
         print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
+    return 0
+
+
+def profile_solve(args, torch):
+    """The solve a DRAM-traffic record of the push is taken on: the same
+    workload, the given options, one warm solve and then the eager solve
+    inside the NVTX range 'profiled'.  Prints the push statistics (links,
+    frontier nodes and hot-page links per launch) of that solve."""
+    from paper_1501_06350_gb300 import _lib, di
+    g = load_workload(args.small)
+    G = di.Graph(g.n, g.ptr, g.idx)
+    st = di.State(G)
+    opts = {}
+    if args.theta is not None:
+        opts["theta_factor"] = args.theta
+    if args.hub_deg is not None:
+        opts["hub_deg"] = args.hub_deg
+    if args.piece is not None:
+        opts["piece"] = args.piece
+    if args.precision == "f32":
+        opts["precision"] = _lib.DI_PREC_F32
+    st.solve(D, tol=TOL, **opts)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("profiled")
+    _, p = st.solve(D, tol=TOL, profile=1, **opts)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    nl = max(p["push_launches"], 1)
+    print(json.dumps({"profile_solve": {"options": opts, "push_launches": p["push_launches"],
+                                        "links_per_launch": p["push_edges"] / nl,
+                                        "nodes_per_launch": p["push_entries"] / nl,
+                                        "hot_links_per_launch": p["push_hot_links"] / nl,
+                                        "sweeps": p["sweeps"]}}), flush=True)
     return 0
 
 

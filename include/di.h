@@ -112,6 +112,8 @@ typedef struct {
     int64_t refinements;     /* DI_PREC_F32: FP64 refinement passes run by this call         */
     int64_t refine_links;    /* DI_PREC_F32: links pushed by those passes                    */
     double resid_inf;        /* max_i |F_i| of the returned state (FP64)                     */
+    int64_t push_hot_links;  /* profile: links of the timed pushes whose target is a hot page
+                                (summed in shared memory, not by a global atomic)           */
 } di_info;
 
 /* Fill *o with the defaults: theta_factor 1, max_sweeps 100000, check_every 8,
@@ -129,6 +131,15 @@ int di_last_cuda_error(void);
 /* Number of CUDA kernels this library has launched in the process so far
    (kernels run by the solver's CUDA-graph loop included).  Diagnostics only. */
 int64_t di_kernel_launches(void);
+
+/* Measured throughput, in 1e9 operations per second, of FP64 atomic additions
+   at random slots of a 32 MB (L2-resident) vector on `device`: 32M additions
+   per launch, a multiplicative hash of the operation index as the slot, best
+   of three timed launches (CUDA events on `stream`) after a warm-up launch.
+   Not a step of the method: every pushed link whose target is not summed in
+   shared memory costs one such addition, so this is the push's roofline.
+   Allocates and frees 32 MB of scratch; returns after the timing. */
+di_status di_probe_atomic_adds(int device, double *gops, void *stream);
 
 /* ---------------------------------------------------------------------------
  * Graph (Section 2.1, Eq. def-p).  P[i][j] = w(j,i) / sum_k w(j,k) for a link

@@ -47,7 +47,7 @@ class di_info(ctypes.Structure):
                 ("push_ms", ctypes.c_double), ("push_launches", ctypes.c_int64),
                 ("push_edges", ctypes.c_int64), ("push_entries", ctypes.c_int64),
                 ("refinements", ctypes.c_int64), ("refine_links", ctypes.c_int64),
-                ("resid_inf", ctypes.c_double)]
+                ("resid_inf", ctypes.c_double), ("push_hot_links", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -74,6 +74,7 @@ SIGNATURES = {
     "di_status_str": (ctypes.c_char_p, [INT]),
     "di_last_cuda_error": (INT, []),
     "di_kernel_launches": (I64, []),
+    "di_probe_atomic_adds": (INT, [INT, ctypes.POINTER(ctypes.c_double), P]),
     "di_graph_create": (INT, [I64, I64, P, P, P, INT, INT, INT, P, ctypes.POINTER(P)]),
     "di_graph_destroy": (INT, [P]),
     "di_graph_info": (INT, [P, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I64),

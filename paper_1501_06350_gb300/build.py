@@ -11,7 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libdi.so")
 BUILD = os.path.join(HERE, "_build")
-UNITS = ["di_prims", "di_graph", "di_solve", "di_update", "di_adjoint", "di_batch", "di_tune", "di_capi", "di_noalloc"]
+UNITS = ["di_prims", "di_graph", "di_solve", "di_update", "di_adjoint", "di_batch", "di_tune", "di_capi", "di_noalloc", "di_probe"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

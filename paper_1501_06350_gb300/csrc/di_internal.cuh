@@ -142,6 +142,7 @@ struct DevCtl {
     unsigned long long max_sweeps;
     unsigned long long npieces;       // hub pieces cut by the plan (read by the push)
     unsigned long long sweep_links;   // links pushed by the running push
+    unsigned long long sweep_hot;     // ... of which into hot pages (summed in shared memory)
     unsigned long long nent;          // frontier nodes of the last selection (mask bits)
     int inf_norm;              // 1: stop test and threshold cap on max |F_i| (adjoint)
     unsigned int done;         // 0 running, 1 converged, 2 sweep cap

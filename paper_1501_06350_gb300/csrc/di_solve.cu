@@ -709,7 +709,7 @@ __global__ void __launch_bounds__(SEL_THREADS)
     // push wrote them, all finished
     const unsigned done0 = __ldcg(&ctl->done);
     int c_inf = 0;
-    unsigned long long c_sweep = 0, c_max_sweeps = 0, c_links = 0, c_pushes = 0, c_diff = 0;
+    unsigned long long c_sweep = 0, c_max_sweeps = 0, c_links = 0, c_hot = 0, c_pushes = 0, c_diff = 0;
     double c_stop = 0.0, c_d = 0.0, c_tf = 0.0, c_cap = 0.0;
     if (threadIdx.x == 0) {
         c_inf = __ldcg(&ctl->inf_norm);
@@ -718,6 +718,7 @@ __global__ void __launch_bounds__(SEL_THREADS)
         c_stop = __ldcg(&ctl->sweep_stop);
         if (blockIdx.x == 0) {
             c_links = __ldcg(&ctl->sweep_links);
+            c_hot = __ldcg(&ctl->sweep_hot);
             c_pushes = __ldcg(&ctl->edge_pushes);
             c_diff = __ldcg(&ctl->diffusions);
             c_d = __ldcg(&ctl->d);
@@ -809,8 +810,12 @@ __global__ void __launch_bounds__(SEL_THREADS)
             // fold the links of the previous push into the totals
             const unsigned long long links = c_links;
             vc->edge_pushes = c_pushes + links;
-            if (stats && sweep >= 1 && sweep <= (unsigned long long)STAT_CAP) stats[2 * (sweep - 1)] = links;
+            if (stats && sweep >= 1 && sweep <= (unsigned long long)STAT_CAP) {
+                stats[3 * (sweep - 1)] = links;
+                stats[3 * (sweep - 1) + 2] = c_hot;
+            }
             vc->sweep_links = 0;
+            vc->sweep_hot = 0;
             vc->l1 = sa;
             // hot_scale >= V / 8, V a bound on what one sweep adds into one
             // page (the push keeps 8 hot_scale of headroom per page).  Plain
@@ -830,7 +835,7 @@ __global__ void __launch_bounds__(SEL_THREADS)
             if (!done) {
                 vc->diffusions = c_diff + sd;
                 vc->nent = sc;
-                if (stats && sweep < (unsigned long long)STAT_CAP) stats[2 * sweep + 1] = sc;
+                if (stats && sweep < (unsigned long long)STAT_CAP) stats[3 * sweep + 1] = sc;
                 double th = c_tf * sa / (double)n;
                 // A sweep that took nothing leaves F unchanged; the largest |F_i|
                 // passes the DI-argmax test exactly, so never ask for more than
@@ -977,7 +982,7 @@ template <typename T, bool WEIGHTED, typename LinkOf>
 __device__ __forceinline__ void scatter_links(unsigned total, LinkOf lane_link, const int32_t *pcol,
                                               const double *w, const float *w32, T *Fd,
                                               unsigned long long *s_hot, const int32_t *hot_node, int hot_shift,
-                                              unsigned long long keep, unsigned long long stream)
+                                              unsigned long long keep, unsigned long long stream, unsigned &hotc)
 {
     const int lane = threadIdx.x & 31;
     for (unsigned base = 0; base < total; base += 128) {
@@ -1004,9 +1009,13 @@ __device__ __forceinline__ void scatter_links(unsigned total, LinkOf lane_link, 
 #pragma unroll
         for (int g = 0; g < 4; g++) {
             if (!ok[g]) continue;
-            if (c[g] >= 0) red_add(Fd + c[g], v[g], keep);
-            else if (!hot_add(s_hot, c[g] & 0x7fffffff, v[g], hot_shift))
-                red_add(Fd + __ldg(hot_node + (c[g] & 0x7fffffff)), v[g], keep);
+            if (c[g] >= 0) {
+                red_add(Fd + c[g], v[g], keep);
+            } else {
+                hotc++;
+                if (!hot_add(s_hot, c[g] & 0x7fffffff, v[g], hot_shift))
+                    red_add(Fd + __ldg(hot_node + (c[g] & 0x7fffffff)), v[g], keep);
+            }
         }
     }
 }
@@ -1037,6 +1046,7 @@ __global__ void __launch_bounds__(PUSH_THREADS, 4)
     constexpr int Q = 4;
     static_assert(Q == 4, "the row pointers of a lane's nodes are one 16-byte load plus one");
     __shared__ unsigned long long s_links[PUSH_THREADS / 32];
+    __shared__ unsigned s_hotc[PUSH_THREADS / 32];
     __shared__ unsigned long long s_hot[HOT_K];   // FP64: fixed point, units of 2^-hot_shift; FP32: floats
     // per warp, the current unit's 128 nodes: link offset of each node inside
     // the unit's link list, its first link, its per-link value
@@ -1068,6 +1078,7 @@ __global__ void __launch_bounds__(PUSH_THREADS, 4)
     const unsigned wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const unsigned nw = (gridDim.x * blockDim.x) >> 5;
     unsigned long long links = 0;
+    unsigned hotc = 0;   // this lane's links into hot pages
     // the mask word of the warp's next unit is loaded one unit ahead
     unsigned mw_next = wid < nunits ? ldnc_u32(mask + (size_t)wid * Q + (lane >> 3), stream) : 0u;
     for (unsigned u = wid; u < nunits + npc; u += nw) {
@@ -1158,7 +1169,8 @@ __global__ void __launch_bounds__(PUSH_THREADS, 4)
                 link = s_row[wq][k] + (e - s_start[wq][k]);
                 vj = s_val[wq][k];
             };
-            scatter_links<T, WEIGHTED>(total, lane_link, pcol, w, w32, Fd, s_hot, hot_node, hot_shift, keep, stream);
+            scatter_links<T, WEIGHTED>(total, lane_link, pcol, w, w32, Fd, s_hot, hot_node, hot_shift, keep, stream,
+                                       hotc);
         } else {
             const unsigned p = u - nunits;
             const Off row = ldnc_u32(pc_row + p, stream), len = ldnc_u32(pc_len + p, stream);
@@ -1168,17 +1180,27 @@ __global__ void __launch_bounds__(PUSH_THREADS, 4)
                 link = row + e;
                 vj = pv;
             };
-            scatter_links<T, WEIGHTED>(len, piece_link, pcol, w, w32, Fd, s_hot, hot_node, hot_shift, keep, stream);
+            scatter_links<T, WEIGHTED>(len, piece_link, pcol, w, w32, Fd, s_hot, hot_node, hot_shift, keep, stream,
+                                       hotc);
         }
     }
-    if (lane == 0) s_links[threadIdx.x >> 5] = links;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) hotc += __shfl_xor_sync(FULL, hotc, o);
+    if (lane == 0) {
+        s_links[threadIdx.x >> 5] = links;
+        s_hotc[threadIdx.x >> 5] = hotc;
+    }
     __syncthreads();
     // one global add per hot page this CTA touched
     for (int k = threadIdx.x; k < nhot; k += PUSH_THREADS) hot_flush(Fd, hot_node, s_hot, k, hot_shift, keep);
     if (threadIdx.x == 0) {
-        unsigned long long t = 0;
-        for (int q = 0; q < PUSH_THREADS / 32; q++) t += s_links[q];
+        unsigned long long t = 0, th = 0;
+        for (int q = 0; q < PUSH_THREADS / 32; q++) {
+            t += s_links[q];
+            th += s_hotc[q];
+        }
         if (t) atomicAdd((unsigned long long *)&ctl->sweep_links, t);
+        if (th) atomicAdd((unsigned long long *)&ctl->sweep_hot, th);
     }
 }
 
@@ -1329,7 +1351,7 @@ di_status state_alloc(di_state_s *st, cudaStream_t s)
     DI_TRY(dalloc_t(&st->tile_l, st->ntiles, s));
     DI_TRY(dalloc_t(&st->ctl, 1, s));
     DI_TRY(dalloc_t(&st->gp, 1, s));
-    DI_TRY(dalloc_t(&st->stats, 2 * STAT_CAP, s));
+    DI_TRY(dalloc_t(&st->stats, 3 * STAT_CAP, s));
     DI_CUDA(cudaMemsetAsync(st->ctl, 0, sizeof(DevCtl), s));
     DI_CUDA(cudaMemsetAsync(st->mask, 0, sizeof(unsigned) * (slots / 32), s));
     DI_CUDA(cudaMemsetAsync(st->F, 0, sizeof(double) * slots, s));
@@ -1639,7 +1661,7 @@ di_status solve_loop(di_graph_s *g, di_state_s *st, double tol, const di_opts *o
     DI_CUDA(cudaGetLastError());
 
     double push_ms = 0.0;
-    int64_t push_launches = 0, push_edges = 0, push_entries = 0;
+    int64_t push_launches = 0, push_edges = 0, push_entries = 0, push_hot = 0;
     int64_t refinements = 0, refine_links = 0;
     if (o->profile && !st->pev) {
         st->pev = new (std::nothrow) cudaEvent_t[2 * STAT_CAP];
@@ -1684,17 +1706,18 @@ di_status solve_loop(di_graph_s *g, di_state_s *st, double tol, const di_opts *o
     if (pp.npairs) {
         // push launch i follows selection i; selections past the converged
         // sweep returned at once and their pushes found no work
-        std::vector<unsigned long long> hstats(2 * STAT_CAP);
+        std::vector<unsigned long long> hstats(3 * STAT_CAP);
         const int ran = (int)((int64_t)hc->sweep < pp.npairs ? (int64_t)hc->sweep : pp.npairs);
-        DI_CUDA(cudaMemcpy(hstats.data(), st->stats, sizeof(unsigned long long) * 2 * ran, cudaMemcpyDeviceToHost));
+        DI_CUDA(cudaMemcpy(hstats.data(), st->stats, sizeof(unsigned long long) * 3 * ran, cudaMemcpyDeviceToHost));
         for (int i = 0; i < ran; i++) {
-            if (hstats[2 * i] == 0) continue;
+            if (hstats[3 * i] == 0) continue;
             float pm = 0.f;
             DI_CUDA(cudaEventElapsedTime(&pm, st->pev[2 * i], st->pev[2 * i + 1]));
             push_ms += pm;
             push_launches++;
-            push_edges += (int64_t)hstats[2 * i];
-            push_entries += (int64_t)hstats[2 * i + 1];
+            push_edges += (int64_t)hstats[3 * i];
+            push_entries += (int64_t)hstats[3 * i + 1];
+            push_hot += (int64_t)hstats[3 * i + 2];
         }
     }
     if (info) {
@@ -1710,6 +1733,7 @@ di_status solve_loop(di_graph_s *g, di_state_s *st, double tol, const di_opts *o
         info->push_launches = push_launches;
         info->push_edges = push_edges;
         info->push_entries = push_entries;
+        info->push_hot_links = push_hot;
         info->refinements = refinements;
         info->refine_links = refine_links;
         info->resid_inf = hc->final_max;

@@ -406,3 +406,14 @@ def test_full_size_web_graph(di):
     assert np.abs(r - Fs).sum() <= 1e-12
     x, _, oinfo, _ = oracle.di_solve(g.n, cp, ci, None, D, tol=1e-12)
     assert np.abs(_np(H) - x).sum() <= 1e-9
+
+
+def test_probe_atomic_adds(di):
+    """The atomic-add ceiling the push is reported against: a plausible rate
+    (the probe times 32M FP64 additions at random slots of a 32 MB vector)."""
+    import ctypes
+    from paper_1501_06350_gb300 import _lib as L
+    g = ctypes.c_double(0.0)
+    L.check(L.lib().di_probe_atomic_adds(torch.cuda.current_device(), ctypes.byref(g), None), "probe")
+    assert 10.0 < g.value < 10_000.0
+    assert L.lib().di_probe_atomic_adds(-1, ctypes.byref(g), None) == L.DI_ERR_INVALID_ARG
