@@ -236,11 +236,18 @@ __device__ __forceinline__ int64_t lower_target(const uint64_t *ukey, int64_t q,
 // counts are prefix differences (ins_pre / del_pre: exclusive counts over the
 // sorted batch) at the row's first entry with target >= c.  One warp per
 // chunk of CH old links, one lane per link.
+//
+// With F given (unweighted graphs), the correction fluid of Theorem update is
+// added here too: column j of d (P' - P) H is d H_j (1/out'(j) - 1/out(j)) at
+// a link kept in the row, -d H_j / out(j) at a deleted one and d H_j / out'(j)
+// at an inserted one (k_merge_ins), one add per link instead of a withdrawal
+// of the old column plus an injection of the new one.
 __global__ void k_merge_old(const uint32_t *ch_row, const uint32_t *ch_idx, const uint64_t *nch_dev,
                             const uint32_t *tlist, const uint32_t *qs, const uint32_t *qes, const Off *rp,
                             const int32_t *col, const double *w, const int32_t *pcol, const Off *nrp,
                             const uint64_t *ukey, const uint8_t *eff, const double *uw, const uint64_t *ins_pre,
-                            const uint64_t *del_pre, int32_t *ncol, double *nw, int32_t *npcol)
+                            const uint64_t *del_pre, int32_t *ncol, double *nw, int32_t *npcol, const double *H,
+                            double d, double *F)
 {
     const int64_t nch = (int64_t)*nch_dev;
     const int lane = threadIdx.x & 31;
@@ -254,11 +261,24 @@ __global__ void k_merge_old(const uint32_t *ch_row, const uint32_t *ch_idx, cons
         const int64_t q = qs[r], qe = qes[r];
         const uint64_t rowkey = (uint64_t)j << 32;
         const Off out0 = nrp[j] - a;
+        double c_keep = 0.0, c_del = 0.0;
+        if (F && i0 < i1) {
+            // the row's two coefficients, one FP64 division pair per chunk
+            if (lane == 0) {
+                const double h = d * H[j];
+                const Off dn = nrp[j + 1] - nrp[j];
+                c_del = -(h / (double)(b - a));
+                c_keep = (dn ? h / (double)dn : 0.0) + c_del;
+            }
+            c_keep = __shfl_sync(FULL, c_keep, 0);
+            c_del = __shfl_sync(FULL, c_del, 0);
+        }
         for (Off i = i0 + lane; i < i1; i += 32) {
             const int32_t c = col[i];
             const int64_t k = lower_target(ukey, q, qe, rowkey | (uint32_t)c);
             unsigned char e = EFF_NOP;
             if (k < qe && (uint32_t)ukey[k] == (uint32_t)c) e = eff[k];
+            if (F) atomicAdd(F + c, e == EFF_DEL ? c_del : c_keep);
             if (e == EFF_DEL) continue;
             const Off out = out0 + i - (Off)(del_pre[k] - del_pre[q]) + (Off)(ins_pre[k] - ins_pre[q]);
             ncol[out] = c;
@@ -285,7 +305,7 @@ __device__ __forceinline__ Off lower_col(const int32_t *col, Off a, Off b, int32
 __global__ void k_merge_ins(const uint64_t *ukey, const uint64_t *nu_dev, const uint8_t *eff, const double *uw,
                             const uint64_t *ins_pre, const uint64_t *del_pre, const uint64_t *tpos, const uint32_t *qs,
                             const Off *rp, const int32_t *col, const int *slot_of, const Off *nrp, int32_t *ncol,
-                            double *nw, int32_t *npcol)
+                            double *nw, int32_t *npcol, const double *H, double d, double *F)
 {
     const int64_t nu = (int64_t)*nu_dev;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nu;
@@ -303,6 +323,7 @@ __global__ void k_merge_ins(const uint64_t *ukey, const uint64_t *nu_dev, const 
             const int sl = slot_of[c];
             npcol[out] = sl >= 0 ? (int32_t)(0x80000000u | (unsigned)sl) : c;
         }
+        if (F) atomicAdd(F + c, d * H[j] / (double)(nrp[j + 1] - nrp[j]));
     }
 }
 
@@ -522,30 +543,43 @@ di_status update_edges(di_graph_s *g, di_state_s *st, int64_t m, const int32_t *
     DI_TRY(t.get(&ncpos, tcap));
     DI_CUDA(cudaMemsetAsync(ocnt, 0, sizeof(uint32_t) * tcap, s));
     DI_CUDA(cudaMemsetAsync(ncnt, 0, sizeof(uint32_t) * tcap, s));
+    // (the new rows' chunks serve only the separate injection of weighted graphs)
+    const bool new_chunks = st && g->weighted;
     k_chunk_counts<<<pgrid, 256, 0, s>>>(tlist, nt_dev, rp, ocnt);
-    k_chunk_counts<<<pgrid, 256, 0, s>>>(tlist, nt_dev, nrp, ncnt);
-    count_launches(2);
+    count_launches(1);
     DI_TRY(scan_exclusive<uint32_t>(ocnt, ocpos, tcap, och_dev, s));
-    DI_TRY(scan_exclusive<uint32_t>(ncnt, ncpos, tcap, nch_dev, s));
+    if (new_chunks) {
+        k_chunk_counts<<<pgrid, 256, 0, s>>>(tlist, nt_dev, nrp, ncnt);
+        count_launches(1);
+        DI_TRY(scan_exclusive<uint32_t>(ncnt, ncpos, tcap, nch_dev, s));
+    }
     // a row of d links has ceil(d / CH) chunks (1 if empty)
     const int64_t ocap = nnz / CH + tcap + 1, ncap = cap / CH + tcap + 1;
-    uint32_t *och_row, *och_idx, *nch_row, *nch_idx;
+    uint32_t *och_row, *och_idx, *nch_row = nullptr, *nch_idx = nullptr;
     DI_TRY(t.get(&och_row, ocap));
     DI_TRY(t.get(&och_idx, ocap));
-    DI_TRY(t.get(&nch_row, ncap));
-    DI_TRY(t.get(&nch_idx, ncap));
     k_chunk_fill<<<pgrid, 256, 0, s>>>(ocnt, ocpos, nt_dev, och_row, och_idx);
-    k_chunk_fill<<<pgrid, 256, 0, s>>>(ncnt, ncpos, nt_dev, nch_row, nch_idx);
-    count_launches(2);
+    count_launches(1);
+    if (new_chunks) {
+        DI_TRY(t.get(&nch_row, ncap));
+        DI_TRY(t.get(&nch_idx, ncap));
+        k_chunk_fill<<<pgrid, 256, 0, s>>>(ncnt, ncpos, nt_dev, nch_row, nch_idx);
+        count_launches(1);
+    }
+    // 6. F += d (P' - P) H.  Unweighted: during the merge, one add per link of
+    // a changed column.  Weighted (W'_j is summed after the merge): the old
+    // columns withdrawn and the new ones injected afterwards.
+    double *fuse_F = (st && !g->weighted) ? st->F : nullptr;
+    const double *fuse_H = st ? st->H : nullptr;
+    const double dd = st ? st->d : 0.0;
     k_merge_old<<<pgrid, 256, 0, s>>>(och_row, och_idx, och_dev, tlist, qs, qe, rp, g->col, g->w, g->pcol, nrp, ukey,
-                                      eff, uw, ins_pre, del_pre, ncol, nwv, npcol);
+                                      eff, uw, ins_pre, del_pre, ncol, nwv, npcol, fuse_H, dd, fuse_F);
     k_merge_ins<<<pgrid, 256, 0, s>>>(ukey, nu_dev, eff, uw, ins_pre, del_pre, tpos, qs, rp, g->col, g->slot_of, nrp,
-                                      ncol, nwv, npcol);
+                                      ncol, nwv, npcol, fuse_H, dd, fuse_F);
     count_launches(2);
     k_row_finish<<<pgrid128, 128, 0, s>>>(tlist, nt_dev, rp, nrp, nwv, nwsum, ddang);
     count_launches(1);
-    // 6. F += d (P' - P) H: withdraw the old columns, inject the new ones
-    if (st) {
+    if (st && g->weighted) {
         k_inject_chunks<<<pgrid, 256, 0, s>>>(och_row, och_idx, och_dev, tlist, rp, g->col, g->w, g->wsum, st->H,
                                              -st->d, st->F);
         k_inject_chunks<<<pgrid, 256, 0, s>>>(nch_row, nch_idx, nch_dev, tlist, nrp, ncol, nwv, nwsum, st->H, st->d,
