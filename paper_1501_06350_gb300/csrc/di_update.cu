@@ -273,17 +273,56 @@ __global__ void k_merge_old(const uint32_t *ch_row, const uint32_t *ch_idx, cons
             c_keep = __shfl_sync(FULL, c_keep, 0);
             c_del = __shfl_sync(FULL, c_del, 0);
         }
-        for (Off i = i0 + lane; i < i1; i += 32) {
-            const int32_t c = col[i];
-            const int64_t k = lower_target(ukey, q, qe, rowkey | (uint32_t)c);
-            unsigned char e = EFF_NOP;
-            if (k < qe && (uint32_t)ukey[k] == (uint32_t)c) e = eff[k];
-            if (F) atomicAdd(F + c, e == EFF_DEL ? c_del : c_keep);
-            if (e == EFF_DEL) continue;
-            const Off out = out0 + i - (Off)(del_pre[k] - del_pre[q]) + (Off)(ins_pre[k] - ins_pre[q]);
-            ncol[out] = c;
-            if (nw) nw[out] = e == EFF_UPD ? uw[k] : w[i];
-            if (npcol) npcol[out] = pcol[i];
+        const int64_t nb = qe - q;
+        if (nb <= 32) {
+            // the row's few batch entries sit in the lanes' registers; a link
+            // counts the deletions and insertions before it by comparing
+            // targets (no searches, no prefix loads)
+            uint32_t tgt = 0;
+            unsigned char ef = EFF_NOP;
+            if (lane < nb) {
+                tgt = (uint32_t)ukey[q + lane];
+                ef = eff[q + lane];
+            }
+            for (Off base = i0; base < i1; base += 32) {
+                const Off i = base + lane;
+                const bool live = i < i1;
+                const int32_t c = live ? col[i] : 0;
+                unsigned dl = 0, in = 0;
+                int km = -1;
+                unsigned char em = EFF_NOP;
+                for (int k = 0; k < (int)nb; k++) {
+                    const uint32_t tk = __shfl_sync(FULL, tgt, k);
+                    const unsigned char ek = (unsigned char)__shfl_sync(FULL, (unsigned)ef, k);
+                    if (tk < (uint32_t)c) {
+                        dl += ek == EFF_DEL;
+                        in += ek == EFF_INS;
+                    } else if (tk == (uint32_t)c) {
+                        km = k;
+                        em = ek;
+                    }
+                }
+                if (!live) continue;
+                if (F) atomicAdd(F + c, em == EFF_DEL ? c_del : c_keep);
+                if (em == EFF_DEL) continue;
+                const Off out = out0 + i - dl + in;
+                ncol[out] = c;
+                if (nw) nw[out] = em == EFF_UPD ? uw[q + km] : w[i];
+                if (npcol) npcol[out] = pcol[i];
+            }
+        } else {
+            for (Off i = i0 + lane; i < i1; i += 32) {
+                const int32_t c = col[i];
+                const int64_t k = lower_target(ukey, q, qe, rowkey | (uint32_t)c);
+                unsigned char e = EFF_NOP;
+                if (k < qe && (uint32_t)ukey[k] == (uint32_t)c) e = eff[k];
+                if (F) atomicAdd(F + c, e == EFF_DEL ? c_del : c_keep);
+                if (e == EFF_DEL) continue;
+                const Off out = out0 + i - (Off)(del_pre[k] - del_pre[q]) + (Off)(ins_pre[k] - ins_pre[q]);
+                ncol[out] = c;
+                if (nw) nw[out] = e == EFF_UPD ? uw[k] : w[i];
+                if (npcol) npcol[out] = pcol[i];
+            }
         }
     }
 }
