@@ -147,21 +147,39 @@ __global__ void k_copy_rows(const Off *rp, const Off *nrp, const int32_t *col, c
         }
         const Off total = __shfl_sync(FULL, incl, 31);
         const Off excl = incl - len;
-        for (Off base = 0; base < total; base += 32) {
-            const Off e = base + lane;
-            const Off eq = e < total ? e : total - 1;
-            int j = 0;
+        // 4 x 32 links in flight per warp: positions first, then the loads,
+        // then the stores
+        for (Off base = 0; base < total; base += 128) {
+            Off from[4], to[4];
 #pragma unroll
-            for (int step = 16; step > 0; step >>= 1) {
-                const Off ex = __shfl_sync(FULL, excl, j + step);
-                if (ex <= eq) j += step;
+            for (int g = 0; g < 4; g++) {
+                const Off e = base + (Off)(32 * g + lane);
+                const Off eq = e < total ? e : total - 1;
+                int j = 0;
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1) {
+                    const Off ex = __shfl_sync(FULL, excl, j + step);
+                    if (ex <= eq) j += step;
+                }
+                const Off o = eq - __shfl_sync(FULL, excl, j);
+                from[g] = __shfl_sync(FULL, a, j) + o;
+                to[g] = __shfl_sync(FULL, na, j) + o;
             }
-            const Off o = eq - __shfl_sync(FULL, excl, j);
-            const Off from = __shfl_sync(FULL, a, j) + o, to = __shfl_sync(FULL, na, j) + o;
-            if (e < total) {
-                ncol[to] = col[from];
-                if (w) nw[to] = w[from];
-                if (npcol) npcol[to] = pcol[from];
+            int32_t c[4], pc[4];
+            double wv[4];
+#pragma unroll
+            for (int g = 0; g < 4; g++) {
+                const bool ok = base + (Off)(32 * g + lane) < total;
+                c[g] = ok ? col[from[g]] : 0;
+                pc[g] = (ok && npcol) ? pcol[from[g]] : 0;
+                wv[g] = (ok && w) ? w[from[g]] : 0.0;
+            }
+#pragma unroll
+            for (int g = 0; g < 4; g++) {
+                if (base + (Off)(32 * g + lane) >= total) continue;
+                ncol[to[g]] = c[g];
+                if (w) nw[to[g]] = wv[g];
+                if (npcol) npcol[to[g]] = pc[g];
             }
         }
     }
@@ -218,6 +236,29 @@ __global__ void k_chunk_fill(const uint32_t *cnt, const uint64_t *cpos, const ui
     }
 }
 
+// The two coefficients of changed row j's column of d (P' - P) H (Theorem
+// update), one thread per changed row: d H_j (1/out'(j) - 1/out(j)) for a kept
+// link and -d H_j / out(j) for a deleted one.  (Computed once per row with
+// every lane busy: FP64 division is slow on this part, and a per-chunk
+// computation by one lane kept the FP64 pipe busy for the whole merge.)
+__global__ void k_row_coef(const uint32_t *tlist, const uint64_t *nt_dev, const Off *rp, const Off *nrp,
+                           const double *H, double d, double2 *coef)
+{
+    const int64_t nt = (int64_t)*nt_dev;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nt;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t j = tlist[k];
+        const Off deg = rp[j + 1] - rp[j], dn = nrp[j + 1] - nrp[j];
+        double c_keep = 0.0, c_del = 0.0;
+        if (deg) {
+            const double h = d * H[j];
+            c_del = -(h / (double)deg);
+            c_keep = (dn ? h / (double)dn : 0.0) + c_del;
+        }
+        coef[k] = make_double2(c_keep, c_del);
+    }
+}
+
 // First batch entry of row j whose target is >= key's, inside [q, qe).
 __device__ __forceinline__ int64_t lower_target(const uint64_t *ukey, int64_t q, int64_t qe, uint64_t key)
 {
@@ -246,8 +287,8 @@ __global__ void k_merge_old(const uint32_t *ch_row, const uint32_t *ch_idx, cons
                             const uint32_t *tlist, const uint32_t *qs, const uint32_t *qes, const Off *rp,
                             const int32_t *col, const double *w, const int32_t *pcol, const Off *nrp,
                             const uint64_t *ukey, const uint8_t *eff, const double *uw, const uint64_t *ins_pre,
-                            const uint64_t *del_pre, int32_t *ncol, double *nw, int32_t *npcol, const double *H,
-                            double d, double *F)
+                            const uint64_t *del_pre, int32_t *ncol, double *nw, int32_t *npcol, const double2 *coef,
+                            double *F)
 {
     const int64_t nch = (int64_t)*nch_dev;
     const int lane = threadIdx.x & 31;
@@ -263,51 +304,60 @@ __global__ void k_merge_old(const uint32_t *ch_row, const uint32_t *ch_idx, cons
         const Off out0 = nrp[j] - a;
         double c_keep = 0.0, c_del = 0.0;
         if (F && i0 < i1) {
-            // the row's two coefficients, one FP64 division pair per chunk
-            if (lane == 0) {
-                const double h = d * H[j];
-                const Off dn = nrp[j + 1] - nrp[j];
-                c_del = -(h / (double)(b - a));
-                c_keep = (dn ? h / (double)dn : 0.0) + c_del;
-            }
-            c_keep = __shfl_sync(FULL, c_keep, 0);
-            c_del = __shfl_sync(FULL, c_del, 0);
+            const double2 cf = coef[r];
+            c_keep = cf.x;
+            c_del = cf.y;
         }
-        const int64_t nb = qe - q;
+        // the batch entries whose targets fall inside this chunk's target range
+        // (all of the row's when it has few): two searches per chunk, by two lanes
+        int64_t klo = q, khi = qe;
+        if (qe - q > 32 && i0 < i1) {
+            int64_t kk = 0;
+            if (lane < 2) {
+                const uint32_t c = (uint32_t)col[lane ? i1 - 1 : i0];
+                kk = lower_target(ukey, q, qe, (rowkey | c) + (uint64_t)lane);
+            }
+            klo = __shfl_sync(FULL, kk, 0);
+            khi = __shfl_sync(FULL, kk, 1);
+        }
+        const int64_t nb = khi - klo;
         if (nb <= 32) {
-            // the row's few batch entries sit in the lanes' registers; a link
-            // counts the deletions and insertions before it by comparing
-            // targets (no searches, no prefix loads)
+            // those few entries sit in the lanes' registers (lane k: entry
+            // klo + k, ascending targets); a link finds how many have a smaller
+            // target by a search over the lanes, and counts the deletions and
+            // insertions among them from two ballots, on top of the row's
+            // counts before the window
+            const Off dl0 = klo > q ? (Off)(del_pre[klo] - del_pre[q]) : 0;
+            const Off in0 = klo > q ? (Off)(ins_pre[klo] - ins_pre[q]) : 0;
             uint32_t tgt = 0;
             unsigned char ef = EFF_NOP;
             if (lane < nb) {
-                tgt = (uint32_t)ukey[q + lane];
-                ef = eff[q + lane];
+                tgt = (uint32_t)ukey[klo + lane];
+                ef = eff[klo + lane];
             }
+            const unsigned dmask = __ballot_sync(FULL, lane < nb && ef == EFF_DEL);
+            const unsigned imask = __ballot_sync(FULL, lane < nb && ef == EFF_INS);
             for (Off base = i0; base < i1; base += 32) {
                 const Off i = base + lane;
                 const bool live = i < i1;
-                const int32_t c = live ? col[i] : 0;
-                unsigned dl = 0, in = 0;
-                int km = -1;
-                unsigned char em = EFF_NOP;
-                for (int k = 0; k < (int)nb; k++) {
-                    const uint32_t tk = __shfl_sync(FULL, tgt, k);
-                    const unsigned char ek = (unsigned char)__shfl_sync(FULL, (unsigned)ef, k);
-                    if (tk < (uint32_t)c) {
-                        dl += ek == EFF_DEL;
-                        in += ek == EFF_INS;
-                    } else if (tk == (uint32_t)c) {
-                        km = k;
-                        em = ek;
-                    }
+                const uint32_t c = live ? (uint32_t)col[i] : 0u;
+                int kk = 0;   // entries with target < c
+#pragma unroll
+                for (int step = 32; step > 0; step >>= 1) {
+                    const uint32_t tk = __shfl_sync(FULL, tgt, (kk + step - 1) & 31);
+                    if (kk + step <= (int)nb && tk < c) kk += step;
                 }
+                const uint32_t tm = __shfl_sync(FULL, tgt, kk & 31);
+                const unsigned char ek = (unsigned char)__shfl_sync(FULL, (unsigned)ef, kk & 31);
+                const bool match = kk < (int)nb && tm == c;
+                const unsigned char em = match ? ek : EFF_NOP;
+                const unsigned below = kk >= 32 ? 0xffffffffu : (1u << kk) - 1u;
                 if (!live) continue;
                 if (F) atomicAdd(F + c, em == EFF_DEL ? c_del : c_keep);
                 if (em == EFF_DEL) continue;
-                const Off out = out0 + i - dl + in;
-                ncol[out] = c;
-                if (nw) nw[out] = em == EFF_UPD ? uw[q + km] : w[i];
+                const Off out = out0 + i - (dl0 + (Off)__popc(dmask & below)) + (in0 + (Off)__popc(imask & below));
+                ncol[out] = (int32_t)c;
+                if (nw) nw[out] = em == EFF_UPD ? uw[klo + kk] : w[i];
                 if (npcol) npcol[out] = pcol[i];
             }
         } else {
@@ -611,8 +661,14 @@ di_status update_edges(di_graph_s *g, di_state_s *st, int64_t m, const int32_t *
     double *fuse_F = (st && !g->weighted) ? st->F : nullptr;
     const double *fuse_H = st ? st->H : nullptr;
     const double dd = st ? st->d : 0.0;
+    double2 *coef = nullptr;
+    if (fuse_F) {
+        DI_TRY(t.get(&coef, tcap));
+        k_row_coef<<<pgrid, 256, 0, s>>>(tlist, nt_dev, rp, nrp, fuse_H, dd, coef);
+        count_launches(1);
+    }
     k_merge_old<<<pgrid, 256, 0, s>>>(och_row, och_idx, och_dev, tlist, qs, qe, rp, g->col, g->w, g->pcol, nrp, ukey,
-                                      eff, uw, ins_pre, del_pre, ncol, nwv, npcol, fuse_H, dd, fuse_F);
+                                      eff, uw, ins_pre, del_pre, ncol, nwv, npcol, coef, fuse_F);
     k_merge_ins<<<pgrid, 256, 0, s>>>(ukey, nu_dev, eff, uw, ins_pre, del_pre, tpos, qs, rp, g->col, g->slot_of, nrp,
                                       ncol, nwv, npcol, fuse_H, dd, fuse_F);
     count_launches(2);

@@ -362,6 +362,68 @@ def test_update_matches_oracle(di, key, frac, cut):
     assert info["converged"] and np.abs(_np(H2) - Hx).sum() <= 1e-9
 
 
+def _dense_row_case(weighted):
+    """A 6,000-page graph whose page 7 links to every even page (about 3,000
+    links, twelve 256-link chunks) and a batch concentrated on that row: 100
+    insertions inside the first chunk's target range, 51 deletions inside the
+    second's, a few changes inside the eighth (after earlier ones, so that
+    chunk starts with non-zero counts), an insertion past the row's last
+    target, an insertion undone later in the batch, and (weighted) a new
+    weight for an existing link; plus scattered changes elsewhere."""
+    n = 6000
+    base = synth.small_graph(n, 30_000, 31, dangling_frac=0.05, weighted=weighted)
+    src = np.repeat(np.arange(n, dtype=np.int64), np.diff(base.ptr))
+    s_all = np.concatenate([src, np.full(3000, 7)])
+    d_all = np.concatenate([base.idx.astype(np.int64), np.arange(0, 6000, 2)])
+    order = np.argsort(s_all, kind="stable")
+    ptr = np.zeros(n + 1, dtype=np.int64)
+    np.add.at(ptr, s_all + 1, 1)
+    ptr = np.cumsum(ptr)
+    idx = d_all[order].astype(np.int32)
+    w = synth.rng_for(91).lognormal(size=len(s_all)).astype(np.float32) if weighted else None
+    cp, ci, cw = oracle.canonical_csr(n, ptr, idx, w)
+    b = [(7, t, 1) for t in range(1, 200, 2)]
+    b += [(7, t, -1) for t in range(600, 701, 2)]
+    b += [(7, 3601, 1), (7, 3602, -1), (7, 3700, -1), (7, 3703, 1), (7, 5999, 1), (7, 301, 1), (7, 301, -1)]
+    if weighted:
+        b += [(7, 1000, 1)]
+    rng = synth.rng_for(92)
+    for _ in range(300):
+        a, t = int(rng.integers(0, n)), int(rng.integers(0, n))
+        if a != t:
+            b.append((a, t, 1 if rng.random() < 0.5 else -1))
+    bs = np.array([x[0] for x in b], dtype=np.int32)
+    bd = np.array([x[1] for x in b], dtype=np.int32)
+    bo = np.array([x[2] for x in b], dtype=np.int8)
+    wb = synth.rng_for(93).lognormal(size=len(b)) if weighted else None
+    return n, ptr, idx, w, (cp, ci, cw), (bs, bd, bo, wb)
+
+
+@pytest.mark.parametrize("weighted", [False, True])
+def test_update_dense_row(di, weighted):
+    # rows whose changes crowd one chunk (more than a warp's worth) and rows
+    # whose chunks start after earlier changes: bit-exact structure, exact
+    # correction fluid, and the resumed solve of P'
+    n, ptr, idx, w, (cp, ci, cw), (bs, bd, bo, wb) = _dense_row_case(weighted)
+    G = di.Graph(n, ptr, idx, w)
+    st = di.State(G)
+    st.solve(D, tol=1e-9)
+    H0, F0, _ = st.export()
+    st.update_edges(bs, bd, bo, wb)
+    p1, i1, w1 = G.export_csr()
+    qp, qi, qw = oracle.apply_batch(n, cp, ci, cw, bs, bd, bo, wb)
+    assert np.array_equal(_np(p1), qp) and np.array_equal(_np(i1), qi)
+    if weighted:
+        assert np.array_equal(_np(w1), qw)
+    H1, F1, _ = st.export()
+    Fo, changed = oracle.update_inject(n, (cp, ci, cw), (qp, qi, qw), D, H0, F0)
+    assert changed > 0
+    assert np.abs(F1 - Fo).sum() <= 1e-13
+    H2, info = st.resume(tol=1e-10 / (1 - D))
+    Hx, _, _, _ = oracle.di_solve(n, qp, qi, qw, D, tol=1e-13)
+    assert info["converged"] and np.abs(_np(H2) - Hx).sum() <= 1e-9
+
+
 def test_update_empty_batch_and_stale_state(di):
     from paper_1501_06350_gb300 import _lib as L
     g = pa10k()
