@@ -333,12 +333,18 @@ __global__ void __launch_bounds__(SEL_THREADS) k_reduce(const double *v, const d
             *reinterpret_cast<float4 *>(v32 + i0 + 4 * q) =
                 make_float4((float)f[4 * q], (float)f[4 * q + 1], (float)f[4 * q + 2], (float)f[4 * q + 3]);
     }
-    double a = fabs(f[0]), mxv = fabs(f[0]);
+    // the largest |f| by the integer order of the magnitude bits (the same as
+    // the FP64 order for non-NaN values; integer compares keep the narrow FP64
+    // pipe of this part for the sum)
+    double a = fabs(f[0]);
+    unsigned long long mxb = abs_bits(f[0]);
 #pragma unroll
     for (int k = 1; k < P; k++) {
         a += fabs(f[k]);
-        mxv = fmax(mxv, fabs(f[k]));
+        const unsigned long long b = abs_bits(f[k]);
+        mxb = b > mxb ? b : mxb;
     }
+    double mxv = __longlong_as_double((long long)mxb);
     double l = 0.0;
     if (H) {
 #pragma unroll
@@ -962,11 +968,38 @@ __device__ __forceinline__ bool hot_add(unsigned long long *s_hot, int slot, flo
     atomicAdd(reinterpret_cast<float *>(s_hot) + slot, v);
     return true;
 }
+// a 2^-sh as the nearest double (ties to even), the same value as
+// scalbn((double)a, -sh), built with integer instructions: the FP64 pipe of
+// this part is narrow, and every CTA converts up to HOT_K sums at its end.
+// |a| < 2^62; a result outside the normal range takes the FP64 route.
+__device__ __forceinline__ double fixed64_to_double(long long a, int sh)
+{
+    if (a == 0) return 0.0;
+    const unsigned long long sgn = a < 0 ? 0x8000000000000000ull : 0ull;
+    const unsigned long long u = a < 0 ? (unsigned long long)(-a) : (unsigned long long)a;
+    int msb = 63 - __clzll((long long)u);
+    unsigned long long mant;
+    if (msb <= 52) {
+        mant = u << (52 - msb);
+    } else {
+        const int s = msb - 52;
+        const unsigned long long rem = u & ((1ull << s) - 1ull), half = 1ull << (s - 1);
+        mant = u >> s;
+        if (rem > half || (rem == half && (mant & 1ull))) mant++;
+        if (mant >> 53) {
+            mant >>= 1;
+            msb++;
+        }
+    }
+    const int be = msb - sh + 1023;
+    if (be < 1 || be > 2046) return scalbn((double)a, -sh);
+    return __longlong_as_double((long long)(sgn | ((unsigned long long)be << 52) | (mant & 0x000fffffffffffffull)));
+}
 __device__ __forceinline__ void hot_flush(double *Fd, const int32_t *hot_node, const unsigned long long *s_hot,
                                           int k, int hot_shift, unsigned long long keep)
 {
     const long long a = (long long)s_hot[k];
-    if (a != 0) red_add_f64(Fd + __ldg(hot_node + k), scalbn((double)a, -hot_shift), keep);
+    if (a != 0) red_add_f64(Fd + __ldg(hot_node + k), fixed64_to_double(a, hot_shift), keep);
 }
 __device__ __forceinline__ void hot_flush(float *Fd, const int32_t *hot_node, const unsigned long long *s_hot,
                                           int k, int, unsigned long long keep)
