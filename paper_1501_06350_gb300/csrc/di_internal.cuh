@@ -234,9 +234,9 @@ constexpr int SEL_THREADS = 512;
 constexpr int SEL_PER_THREAD = 16;
 constexpr int TILE = SEL_THREADS * SEL_PER_THREAD;   // nodes per selection tile
 // Row-pointer arrays read by the push carry RP_PAD zeroed entries past rp[n]:
-// a lane whose four nodes include a selected one loads all five row pointers
-// of the four, which reaches rp[n + 3] in the last unit.
-constexpr int RP_PAD = 3;
+// the push stages the 129 row pointers of a whole 128-page unit, which reaches
+// rp[n + 127] for the unit that holds page n - 1.
+constexpr int RP_PAD = 128;
 // Links per bucket of the row lookup table (row_bucket_table).
 constexpr int KEY_BUCKET_SHIFT = 8;
 constexpr int PUSH_THREADS = 256;
