@@ -45,8 +45,12 @@ void dfree(void *p, cudaStream_t s)
 // synchronisation, so each graph build, update or solve with host inputs
 // mapped and unmapped its temporaries again (about 3 ms of a 4M-page build).
 // Keeping up to POOL_KEEP bytes of freed memory in the pool (an attribute of
-// this process's pool, gone with the process) lets them be reused.
-constexpr uint64_t POOL_KEEP = 2ull << 30;
+// this process's pool, gone with the process) lets them be reused.  The bound
+// is sized for the largest graphs this library targets on a 288 GB part: a
+// link update of a 557M-link graph allocates its new 2.2 GB link arrays while
+// the old ones are still live, and with a 2 GiB bound those pages were mapped
+// afresh at every update (about 10 ms of a 25 ms update).
+constexpr uint64_t POOL_KEEP = 16ull << 30;
 void pool_keep(int device)
 {
     static bool done[64] = {};

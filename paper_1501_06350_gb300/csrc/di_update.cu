@@ -211,14 +211,17 @@ __global__ void k_row_ranges(const uint64_t *ukey, const uint64_t *nu_dev, const
 // is one chunk), so that a long row is merged and injected by many threads.
 constexpr Off CH = 256;
 
-__global__ void k_chunk_counts(const uint32_t *tlist, const uint64_t *nt_dev, const Off *rp, uint32_t *cnt)
+// (Rows of at most `short_max` links get no chunk: k_merge_short handles them.)
+__global__ void k_chunk_counts(const uint32_t *tlist, const uint64_t *nt_dev, const Off *rp, uint32_t *cnt,
+                               Off short_max)
 {
     const int64_t nt = (int64_t)*nt_dev;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nt;
          k += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t j = tlist[k];
         const Off deg = rp[j + 1] - rp[j];
-        cnt[k] = deg == 0 ? 1u : (uint32_t)((deg + CH - 1) / CH);
+        if (short_max && deg <= short_max) cnt[k] = 0u;
+        else cnt[k] = deg == 0 ? 1u : (uint32_t)((deg + CH - 1) / CH);
     }
 }
 
@@ -373,6 +376,79 @@ __global__ void k_merge_old(const uint32_t *ch_row, const uint32_t *ch_idx, cons
                 if (nw) nw[out] = e == EFF_UPD ? uw[k] : w[i];
                 if (npcol) npcol[out] = pcol[i];
             }
+        }
+    }
+}
+
+// The changed rows of at most CH old links (unweighted graphs), 32 rows per
+// warp: lane l reads row tlist[32g + l] (its bounds, batch range and
+// coefficients) and the links of the 32 rows are dealt to the lanes 32 at a
+// time, so that the chain of dependent loads that starts a row is paid once
+// per 32 rows rather than once per row.  A link's place and correction fluid
+// are those of k_merge_old (its row's batch entries searched in global memory:
+// a short row has few).
+__global__ void k_merge_short(const uint32_t *tlist, const uint64_t *nt_dev, const uint32_t *qs,
+                              const uint32_t *qes, const Off *rp, const int32_t *col, const int32_t *pcol,
+                              const Off *nrp, const uint64_t *ukey, const uint8_t *eff, const uint64_t *ins_pre,
+                              const uint64_t *del_pre, int32_t *ncol, int32_t *npcol, const double2 *coef,
+                              double *F)
+{
+    const int64_t nt = (int64_t)*nt_dev;
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t gi = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; gi * 32 < nt; gi += nwarp) {
+        const int64_t k = gi * 32 + lane;
+        uint32_t j = 0, q = 0, qe = 0;
+        Off a = 0, len = 0, out0 = 0;
+        double c_keep = 0.0, c_del = 0.0;
+        if (k < nt) {
+            j = tlist[k];
+            a = rp[j];
+            const Off b = rp[j + 1];
+            if (b - a <= CH) {
+                len = b - a;
+                q = qs[k];
+                qe = qes[k];
+                out0 = nrp[j] - a;
+                if (F && len) {
+                    const double2 cf = coef[k];
+                    c_keep = cf.x;
+                    c_del = cf.y;
+                }
+            }
+        }
+        Off incl = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const Off y = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const Off total = __shfl_sync(FULL, incl, 31);
+        const Off excl = incl - len;
+        for (Off base = 0; base < total; base += 32) {
+            const Off e = base + lane;
+            const Off eq = e < total ? e : total - 1;
+            int r = 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                const Off ex = __shfl_sync(FULL, excl, r + step);
+                if (ex <= eq) r += step;
+            }
+            const Off i = __shfl_sync(FULL, a, r) + (eq - __shfl_sync(FULL, excl, r));
+            const uint32_t jr = __shfl_sync(FULL, j, r);
+            const uint32_t qr = __shfl_sync(FULL, q, r), qer = __shfl_sync(FULL, qe, r);
+            const Off o0 = __shfl_sync(FULL, out0, r);
+            const double ck = __shfl_sync(FULL, c_keep, r), cd = __shfl_sync(FULL, c_del, r);
+            if (e >= total) continue;
+            const int32_t c = col[i];
+            const int64_t kq = lower_target(ukey, qr, qer, ((uint64_t)jr << 32) | (uint32_t)c);
+            unsigned char em = EFF_NOP;
+            if (kq < (int64_t)qer && (uint32_t)ukey[kq] == (uint32_t)c) em = eff[kq];
+            if (F) atomicAdd(F + c, em == EFF_DEL ? cd : ck);
+            if (em == EFF_DEL) continue;
+            const Off out = o0 + i - (Off)(del_pre[kq] - del_pre[qr]) + (Off)(ins_pre[kq] - ins_pre[qr]);
+            ncol[out] = c;
+            if (npcol) npcol[out] = pcol[i];
         }
     }
 }
@@ -634,11 +710,15 @@ di_status update_edges(di_graph_s *g, di_state_s *st, int64_t m, const int32_t *
     DI_CUDA(cudaMemsetAsync(ncnt, 0, sizeof(uint32_t) * tcap, s));
     // (the new rows' chunks serve only the separate injection of weighted graphs)
     const bool new_chunks = st && g->weighted;
-    k_chunk_counts<<<pgrid, 256, 0, s>>>(tlist, nt_dev, rp, ocnt);
+    // unweighted graphs: rows of at most CH old links are merged 32 to a warp
+    // (k_merge_short); weighted graphs chunk every row (the old columns are
+    // also withdrawn per chunk)
+    const Off short_max = g->weighted ? 0 : CH;
+    k_chunk_counts<<<pgrid, 256, 0, s>>>(tlist, nt_dev, rp, ocnt, short_max);
     count_launches(1);
     DI_TRY(scan_exclusive<uint32_t>(ocnt, ocpos, tcap, och_dev, s));
     if (new_chunks) {
-        k_chunk_counts<<<pgrid, 256, 0, s>>>(tlist, nt_dev, nrp, ncnt);
+        k_chunk_counts<<<pgrid, 256, 0, s>>>(tlist, nt_dev, nrp, ncnt, 0);
         count_launches(1);
         DI_TRY(scan_exclusive<uint32_t>(ncnt, ncpos, tcap, nch_dev, s));
     }
@@ -665,6 +745,11 @@ di_status update_edges(di_graph_s *g, di_state_s *st, int64_t m, const int32_t *
     if (fuse_F) {
         DI_TRY(t.get(&coef, tcap));
         k_row_coef<<<pgrid, 256, 0, s>>>(tlist, nt_dev, rp, nrp, fuse_H, dd, coef);
+        count_launches(1);
+    }
+    if (short_max) {
+        k_merge_short<<<pgrid, 256, 0, s>>>(tlist, nt_dev, qs, qe, rp, g->col, g->pcol, nrp, ukey, eff, ins_pre, del_pre,
+                                            ncol, npcol, coef, fuse_F);
         count_launches(1);
     }
     k_merge_old<<<pgrid, 256, 0, s>>>(och_row, och_idx, och_dev, tlist, qs, qe, rp, g->col, g->w, g->pcol, nrp, ukey,
