@@ -245,7 +245,7 @@ constexpr int DTAB_MAX = 65536;                      // out-degrees with a tabul
 constexpr int PIECE = 1024;                          // default links per hub piece (di_opts.piece)
 constexpr int RED_THREADS = 256;
 constexpr int STAT_CAP = 4096;                       // sweeps with recorded statistics
-constexpr int PLAN_CTAS = 32;                        // CTAs of the per-sweep plan kernel
+constexpr int PLAN_CTAS = 64;                        // CTAs of the per-sweep plan kernel
 constexpr int HOT_K = 2048;                          // pages accumulated in shared memory by the push
 constexpr unsigned HOT_MIN_INDEG = 64;               // ... if they have at least this many in-links
 

@@ -704,7 +704,7 @@ __global__ void __launch_bounds__(SEL_THREADS, sizeof(T) == 8 ? SEL_CTAS : 1)
 // (SUB) takes from D, adds to H, and lands in the FP64 fluid F, from which it
 // also subtracts the taken amount: F + d P D - D.
 template <typename T, bool SUB>
-__global__ void __launch_bounds__(SEL_THREADS)
+__global__ void __launch_bounds__(SEL_THREADS, 1)
     k_plan(T *Ft, T *Fd, double *Hs, const GraphPtrs *__restrict__ gp, const double *__restrict__ dscale,
            int64_t n, int64_t ntiles, const unsigned *tile_cnt, const unsigned *tile_diff, const float *tile_l1f,
            const unsigned *tile_maxf, const unsigned *tile_maxu, const uint64_t *__restrict__ hub_base,
@@ -912,12 +912,25 @@ __global__ void __launch_bounds__(SEL_THREADS)
             unsigned long long wbase = 0;
             if (lane == 31 && wtot) wbase = atomicAdd((unsigned long long *)&ctl->npieces, (unsigned long long)wtot);
             wbase = __shfl_sync(FULL, wbase, 31);
-            unsigned long long pb = wbase + incl - np;
-            for (Off o = 0; o < deg; o += piece) {
-                pc_row[pb] = t.r0 + o;
-                pc_len[pb] = deg - o < piece ? deg - o : piece;
-                pc_val[pb] = v;
-                pb++;
+            // the warp's pieces written 32 at a time, one per lane (a hub of
+            // 50,000 links has about a hundred: one lane writing them all was
+            // the plan's longest chain)
+            const unsigned excl = incl - np;
+            for (unsigned b0 = 0; b0 < wtot; b0 += 32) {
+                const unsigned e = b0 + lane;
+                const unsigned eq = e < wtot ? e : wtot - 1;
+                int h = 0;   // the lane whose hub holds piece eq
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1)
+                    if (__shfl_sync(FULL, excl, h + step) <= eq) h += step;
+                const Off r0 = __shfl_sync(FULL, t.r0, h), dh = __shfl_sync(FULL, deg, h);
+                const double vh = __shfl_sync(FULL, v, h);
+                const Off o = (eq - __shfl_sync(FULL, excl, h)) * piece;
+                if (e < wtot) {
+                    pc_row[wbase + e] = r0 + o;
+                    pc_len[wbase + e] = dh - o < piece ? dh - o : piece;
+                    pc_val[wbase + e] = vh;
+                }
             }
         }
     }
