@@ -424,6 +424,63 @@ def test_update_dense_row(di, weighted):
     assert info["converged"] and np.abs(_np(H2) - Hx).sum() <= 1e-9
 
 
+@pytest.mark.parametrize("weighted", [False, True])
+def test_update_row_length_boundaries(di, weighted):
+    # changed rows whose old length sits on either side of the 32-link warp
+    # batch and the 256-link chunk (the merge takes rows of up to 256 links 32
+    # to a warp and longer ones by chunks), each with changes at its start, at
+    # its end, past its last target and around link 256
+    n = 4000
+    base = synth.small_graph(n, 12_000, 41, dangling_frac=0.05, weighted=weighted)
+    lens = {11: 31, 12: 32, 13: 255, 14: 256, 15: 257, 16: 513, 17: 0}
+    keep = ~np.isin(np.repeat(np.arange(n), np.diff(base.ptr)), list(lens))
+    src = np.repeat(np.arange(n, dtype=np.int64), np.diff(base.ptr))[keep]
+    dst = base.idx.astype(np.int64)[keep]
+    for r, L in lens.items():
+        src = np.concatenate([src, np.full(L, r)])
+        dst = np.concatenate([dst, 3 * np.arange(L) + 3])
+    order = np.argsort(src, kind="stable")
+    ptr = np.zeros(n + 1, dtype=np.int64)
+    np.add.at(ptr, src + 1, 1)
+    ptr = np.cumsum(ptr)
+    idx = dst[order].astype(np.int32)
+    w = synth.rng_for(94).lognormal(size=len(idx)).astype(np.float32) if weighted else None
+    cp, ci, cw = oracle.canonical_csr(n, ptr, idx, w)
+    b = []
+    for r, L in lens.items():
+        b += [(r, 1, 1), (r, 3 * L + 4, 1)]                      # before the first, past the last
+        if L:
+            b += [(r, 3, -1), (r, 3 * L, -1)]                    # the first and the last link
+        if L > 256:
+            b += [(r, 3 * 256, -1), (r, 3 * 256 + 1, 1), (r, 3 * 257 + 2, 1)]
+    rng = synth.rng_for(95)
+    for _ in range(200):
+        a, t = int(rng.integers(0, n)), int(rng.integers(0, n))
+        if a != t:
+            b.append((a, t, 1 if rng.random() < 0.5 else -1))
+    bs = np.array([x[0] for x in b], dtype=np.int32)
+    bd = np.array([x[1] for x in b], dtype=np.int32)
+    bo = np.array([x[2] for x in b], dtype=np.int8)
+    wb = synth.rng_for(96).lognormal(size=len(b)) if weighted else None
+    G = di.Graph(n, ptr, idx, w)
+    st = di.State(G)
+    st.solve(D, tol=1e-9)
+    H0, F0, _ = st.export()
+    st.update_edges(bs, bd, bo, wb)
+    p1, i1, w1 = G.export_csr()
+    qp, qi, qw = oracle.apply_batch(n, cp, ci, cw, bs, bd, bo, wb)
+    assert np.array_equal(_np(p1), qp) and np.array_equal(_np(i1), qi)
+    if weighted:
+        assert np.array_equal(_np(w1), qw)
+    H1, F1, _ = st.export()
+    Fo, changed = oracle.update_inject(n, (cp, ci, cw), (qp, qi, qw), D, H0, F0)
+    assert changed > 0
+    assert np.abs(F1 - Fo).sum() <= 1e-13
+    H2, info = st.resume(tol=1e-10 / (1 - D))
+    Hx, _, _, _ = oracle.di_solve(n, qp, qi, qw, D, tol=1e-13)
+    assert info["converged"] and np.abs(_np(H2) - Hx).sum() <= 1e-9
+
+
 def test_update_empty_batch_and_stale_state(di):
     from paper_1501_06350_gb300 import _lib as L
     g = pa10k()
