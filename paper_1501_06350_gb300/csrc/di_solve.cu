@@ -990,14 +990,7 @@ __device__ __forceinline__ bool hot_add(unsigned long long *s_hot, int slot, dou
     const int ex = (int)(((unsigned long long)__double_as_longlong(v) >> 52) & 0x7ffu);
     if (ex == 0) return v == 0.0;   // a subnormal contribution goes to global memory as it is
     if (ex - 1023 + hot_shift > 58) return false;
-    // the 64-bit sum as two 32-bit shared atomics: the low word's add returns
-    // the old value, its carry goes into the high word with the high part (the
-    // same sum modulo 2^64, read back as one 64-bit word)
-    const unsigned long long q = (unsigned long long)to_fixed64(v, hot_shift);
-    unsigned *wd = reinterpret_cast<unsigned *>(s_hot + slot);
-    const unsigned lo = (unsigned)q, old = atomicAdd(wd, lo);
-    const unsigned hi = (unsigned)(q >> 32) + (old + lo < old ? 1u : 0u);
-    if (hi) atomicAdd(wd + 1, hi);
+    atomicAdd(s_hot + slot, (unsigned long long)to_fixed64(v, hot_shift));
     return true;
 }
 __device__ __forceinline__ bool hot_add(unsigned long long *s_hot, int slot, float v, int)
