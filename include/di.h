@@ -25,9 +25,10 @@
  *  - Handles are not thread-safe: one host thread per handle at a time.
  *  - Device scratch comes from the device's default stream-ordered memory
  *    pool (cudaMallocAsync).  The first di_graph_create on a device sets that
- *    pool's release threshold to 2 GiB, so up to 2 GiB of freed scratch stays
- *    mapped for reuse by later calls instead of being unmapped at every
- *    synchronisation; it is an attribute of this process's pool only.  The
+ *    pool's release threshold to 16 GiB, so up to 16 GiB of freed scratch and
+ *    replaced link arrays stays mapped for reuse by later calls instead of
+ *    being unmapped at every synchronisation; it is an attribute of this
+ *    process's pool only.  The
  *    allocation-free entry point di_residual_l1_noalloc allocates nothing.
  */
 #ifndef DI_H

@@ -49,7 +49,7 @@ void dfree(void *p, cudaStream_t s)
 // is sized for the largest graphs this library targets on a 288 GB part: a
 // link update of a 557M-link graph allocates its new 2.2 GB link arrays while
 // the old ones are still live, and with a 2 GiB bound those pages were mapped
-// afresh at every update (about 10 ms of a 25 ms update).
+// afresh at every update.
 constexpr uint64_t POOL_KEEP = 16ull << 30;
 void pool_keep(int device)
 {
